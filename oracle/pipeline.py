@@ -1,0 +1,122 @@
+"""Units, evaluation and assembly (oracle).
+
+A unit is one (sector, eps order K) pair, integrated on its own, as in the
+paper's integrand database whose keys carry the eps order and the sector number
+(Sec. 4.7).  Per order, sector results are summed and their errors combined in
+the mean-square norm, sqrt(sum sigma^2) (Sec. 4.3); the prefactor series is then
+multiplied in (Eq. 2).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import sympy as sp
+import mpmath as mp
+
+from . import sectors as S
+from .uf import symanzik
+from .prefactor import prefactor_series, combine
+
+
+@dataclasses.dataclass
+class Unit:
+    sector: int                 # index into the sector list
+    order: int                  # eps order K of the parametric integral
+    variables: tuple            # original indices; dimension i of the cube <-> variables[i]
+    expr: object                # sympy expression in t-symbols
+    _np: object = None
+    _mp: object = None
+
+    @property
+    def dim(self):
+        return len(self.variables)
+
+    def f_numpy(self, X):
+        """Evaluate in float64 at points X of shape (n, dim)."""
+        if self._np is None:
+            syms = [S.tsym(j) for j in self.variables]
+            self._np = sp.lambdify(syms, self.expr, modules="numpy")
+        cols = [X[:, i] for i in range(self.dim)]
+        with np.errstate(all="ignore"):
+            v = self._np(*cols)
+        return np.broadcast_to(np.asarray(v, dtype=np.float64), (X.shape[0],)).copy()
+
+    def f_mp(self, x, dps=50):
+        """Evaluate at one point with mpmath at ``dps`` digits (x given as exact binary64)."""
+        if self._mp is None:
+            syms = [S.tsym(j) for j in self.variables]
+            self._mp = sp.lambdify(syms, self.expr, modules="mpmath")
+        with mp.workdps(dps):
+            return self._mp(*[mp.mpf(float(v)) for v in x])
+
+
+@dataclasses.dataclass
+class Problem:
+    name: str
+    sectors: list
+    units: list
+    prefactor: tuple          # (q, coeffs)
+    int_orders: tuple         # orders K of the parametric integral
+    out_orders: tuple         # orders n of the final result
+
+
+def feynman_problem(problem, strategy="M"):
+    U, F, xs = symanzik(problem)
+    L = len(problem.loop_momenta)
+    prim = S.primary_sectors(U, F, xs, problem.indices, L)
+    secs = [s for p in prim for s in S.decompose(p, strategy)]
+    kmin = min(S.min_order(s) for s in secs)
+    q0, _ = prefactor_series(problem.indices, L, 0)
+    khi = problem.order + q0
+    pre = prefactor_series(problem.indices, L, problem.order - kmin)
+    units = []
+    for i, s in enumerate(secs):
+        for K in range(max(kmin, S.min_order(s)), khi + 1):
+            e = S.unit_integrand(s, K)
+            if e != 0:
+                units.append(Unit(i, K, s.variables, e))
+    int_orders = tuple(range(kmin, khi + 1))
+    out_orders = tuple(range(kmin - pre[0], problem.order + 1))
+    return Problem(problem.name, secs, units, pre, int_orders, out_orders)
+
+
+def direct_problem(problem):
+    sec = S.direct_sector(problem)
+    secs = S.decompose(sec, "M")
+    units = []
+    for i, s in enumerate(secs):
+        for K in problem.orders:
+            if K < S.min_order(s):
+                continue
+            e = S.unit_integrand(s, K)
+            if e != 0:
+                units.append(Unit(i, K, s.variables, e))
+    return Problem(problem.name, secs, units, (0, [mp.mpf(1)]), tuple(problem.orders), tuple(problem.orders))
+
+
+def sum_orders(prob, unit_values, unit_errors=None):
+    """Per eps order: sum over sectors; errors in the mean-square norm."""
+    val = {K: 0.0 for K in prob.int_orders}
+    err = {K: 0.0 for K in prob.int_orders}
+    for i, u in enumerate(prob.units):
+        val[u.order] += unit_values[i]
+        if unit_errors is not None:
+            err[u.order] += unit_errors[i] ** 2
+    return val, {K: math.sqrt(e) for K, e in err.items()}
+
+
+def assemble(prob, val, err):
+    """Multiply the prefactor series in; sigma_n = sqrt(sum c_m^2 sigma_{n-m}^2)."""
+    R = combine(prob.prefactor, prob.int_orders, val, prob.out_orders)
+    q, coeffs = prob.prefactor
+    E = {}
+    for n in prob.out_orders:
+        s = 0.0
+        for i, c in enumerate(coeffs):
+            K = n - (i - q)
+            if K in err:
+                s += float(c) ** 2 * err[K] ** 2
+        E[n] = math.sqrt(s)
+    return {n: float(v) for n, v in R.items()}, E

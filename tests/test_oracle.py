@@ -1,0 +1,304 @@
+"""Pins of the oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: every expected value comes from a
+closed form, a textbook polynomial, the paper's printed example, published
+known-answer vectors, an invariant, or an independent library routine.
+"""
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+import sympy as sp
+
+import workloads as W
+from oracle import pipeline as P, quadrature as Q, sectors as S, vegas as V
+from oracle.philox import philox4x32_10, uniforms as philox_uniforms
+from oracle.prefactor import prefactor_series
+from oracle.sobol import primitive_polynomials, sobol_ints, uniforms as sobol_uniforms
+from oracle.uf import symanzik
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _quad_problem(pr, h=1 / 12, smax=3.0):
+    vals = [Q.integrate_box(u.f_numpy, u.dim, h=h, smax=smax) for u in pr.units]
+    val, err = P.sum_orders(pr, vals)
+    R, _ = P.assemble(pr, val, err)
+    return val, R
+
+
+# --------------------------------------------------------------------------- UF
+
+def test_uf_bubble_and_box():
+    U, F, x = symanzik(W.bubble())
+    assert sp.expand(U - (x[0] + x[1])) == 0
+    assert sp.expand(F - x[0] * x[1]) == 0            # F = (-p^2) x1 x2 at p^2 = -1
+    U, F, x = symanzik(W.box())                        # S = 1, T = 2
+    assert sp.expand(U - sum(x)) == 0
+    assert sp.expand(F - (x[0] * x[2] + 2 * x[1] * x[3])) == 0
+    U, F, x = symanzik(W.box_paper_example())          # S = 3, T = 1
+    assert sp.expand(F - (3 * x[0] * x[2] + x[1] * x[3])) == 0
+
+
+def test_uf_double_box_textbook_U_and_routing():
+    U, F, x = symanzik(W.double_box())
+    x1, x2, x3, x4, x5, x6, x7 = x
+    # spanning trees of the ladder: (x1+x2+x3)(x5+x6+x7) + x4 (x1+x2+x3+x5+x6+x7)
+    assert sp.expand(U - ((x1 + x2 + x3) * (x5 + x6 + x7) + x4 * (x1 + x2 + x3 + x5 + x6 + x7))) == 0
+    U2, F2, _ = symanzik(W.double_box_alt_routing())
+    assert sp.expand(U - U2) == 0 and sp.expand(F - F2) == 0
+    # the t-channel part of the planar ladder is a single 2-forest through the rung x4
+    Ft, _, _ = symanzik(W.double_box(S=0, T=1))[1], None, None
+    Ft = symanzik(W.double_box(S=0, T=1))[1]
+    terms = sp.Add.make_args(sp.expand(Ft))
+    assert len(terms) == 1 and x4 in terms[0].free_symbols
+    assert all(c > 0 for c in sp.Poly(F, *x).coeffs())
+
+
+# --------------------------------------------------------------------- prefactor
+
+def test_prefactor_gamma_series():
+    # e^{gamma eps} Gamma(1+eps) = exp(sum_{k>=2} (-1)^k zeta(k) eps^k / k)  (textbook)
+    q, c = prefactor_series((1, 1), 1, 4)
+    assert q == 1
+    with mp.workdps(30):
+        z = [0, 0] + [(-1) ** k * mp.zeta(k) / k for k in range(2, 7)]
+        expo = mp.taylor(lambda e: mp.exp(sum(z[k] * e ** k for k in range(2, 7))), 0, 5)
+    for i in range(5):
+        assert abs(c[i] - expo[i]) < 1e-25
+    q, c = prefactor_series((1,) * 7, 2, 2)
+    assert q == 0 and abs(c[0] - 2) < 1e-25              # Gamma(3) for the double box
+
+
+# ------------------------------------------------------- closed forms, end to end
+
+def test_bubble_closed_form():
+    pr = P.feynman_problem(W.bubble(order=2))
+    _, R = _quad_problem(pr)
+    with mp.workdps(30):
+        f = lambda e: e * mp.exp(mp.euler * e) * mp.gamma(e) * mp.gamma(1 - e) ** 2 / mp.gamma(2 - 2 * e)
+        c = mp.taylor(f, 0, 3, method="quad", radius=0.25)
+    for n in range(-1, 3):
+        assert abs(R[n] - float(c[n + 1])) < 1e-10, (n, R[n], c[n + 1])
+    # FIESTA normalisation values 1, 2, 4 - pi^2/12, 8 - pi^2/6 - 7 zeta3 / 3
+    z3 = float(mp.zeta(3))
+    exact = [1.0, 2.0, 4 - math.pi ** 2 / 12, 8 - math.pi ** 2 / 6 - 7 * z3 / 3]
+    for n in range(-1, 3):
+        assert abs(R[n] - exact[n + 1]) < 1e-10
+
+
+def _box_closed(S_, T_):
+    """Textbook one-loop massless box through eps^0 in this normalisation."""
+    with mp.workdps(30):
+        S_, T_ = mp.mpf(S_), mp.mpf(T_)
+        def g(e):
+            cg = mp.exp(mp.euler * e) * mp.gamma(1 + e) * mp.gamma(1 - e) ** 2 / mp.gamma(1 - 2 * e)
+            return cg / (S_ * T_) * (2 * (S_ ** (-e) + T_ ** (-e)) - e ** 2 * (mp.log(S_ / T_) ** 2 + mp.pi ** 2))
+        c = mp.taylor(g, 0, 2, method="quad", radius=0.25)
+    return {-2: float(c[0]), -1: float(c[1]), 0: float(c[2])}
+
+
+@pytest.mark.parametrize("S_,T_", [(1, 2), (3, 1)])
+def test_box_closed_form(S_, T_):
+    pr = P.feynman_problem(W.box(S=S_, T=T_))
+    _, R = _quad_problem(pr)
+    ref = _box_closed(S_, T_)
+    for n in (-2, -1, 0):
+        assert abs(R[n] - ref[n]) < 1e-9, (n, R[n], ref[n])
+    if (S_, T_) == (1, 2):
+        assert abs(R[-2] - 2) < 1e-9 and abs(R[-1] + math.log(2)) < 1e-9
+        assert abs(R[0] + 2 * math.pi ** 2 / 3) < 1e-9
+
+
+def test_box_matches_paper_example():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "box_S3_T1_paper.txt")) if l.strip() and l[0] != "#"]
+    pr = P.feynman_problem(W.box_paper_example())
+    _, R = _quad_problem(pr)
+    for order, value, err in rows:
+        order, value, err = int(order), float(value), float(err)
+        digits = len(value.__repr__().split(".")[1]) if "." in repr(value) else 0
+        tol = 3 * err + 0.5 * 10 ** (-digits)
+        assert abs(R[order] - value) <= tol, (order, R[order], value, tol)
+
+
+def test_strategy_invariance_box():
+    sums = {}
+    for strat in ("X", "Xrev", "M", "R"):
+        pr = P.feynman_problem(W.box(), strategy=strat)
+        sums[strat], _ = _quad_problem(pr)
+    paths = {strat: None for strat in sums}
+    for strat in sums:
+        for K in (-2, -1, 0):
+            assert abs(sums[strat][K] - sums["X"][K]) < 1e-9
+    # the strategies really decompose differently
+    U, F, xs = symanzik(W.box())
+    lists = {}
+    for strat in ("X", "Xrev"):
+        prim = S.primary_sectors(U, F, xs, (1, 1, 1, 1), 1)
+        lists[strat] = [s.path for p in prim for s in S.decompose(p, strat)]
+    assert lists["X"] != lists["Xrev"]
+
+
+def test_bubble_sector_symmetry_and_1d_mpmath():
+    pr = P.feynman_problem(W.bubble())
+    by = {}
+    for u in pr.units:
+        by.setdefault(u.order, []).append(u)
+    for K, us in by.items():
+        assert len(us) == 2
+        with mp.workdps(25):
+            a = mp.quad(lambda t: us[0].f_mp([t], 25), [0, 1])
+            b = mp.quad(lambda t: us[1].f_mp([t], 25), [0, 1])
+        assert abs(a - b) < 1e-18
+        tq = Q.integrate_box(us[0].f_numpy, 1)
+        assert abs(tq - float(a)) < 1e-12
+    # raw eps^1 sum: 2 * int (1+t)^-2 (2 ln(1+t) - ln t) dt = 2
+    s1 = sum(Q.integrate_box(u.f_numpy, 1) for u in by[1])
+    assert abs(s1 - 2.0) < 1e-12
+
+
+def test_higher_pole_subtraction():
+    """int_0^1 t^{-2+eps} / (1+t) dt, p = 1 Taylor subtraction, vs the digamma closed form."""
+    t1 = S.tsym(1)
+    sec = S.Sector(0, (1,), sp.Integer(1), {1: (-2, 1)}, [(sp.Poly(1 + t1, t1), (-1, 0))])
+    # beta(s) = int_0^1 t^{s-1}/(1+t) dt = (psi((s+1)/2) - psi(s/2))/2, s = -1 + eps
+    with mp.workdps(30):
+        f = lambda e: e * (mp.digamma(e / 2) - mp.digamma((e - 1) / 2)) / 2
+        c = mp.taylor(f, 0, 3, method="quad", radius=0.25)
+    for K in range(-1, 3):
+        e = S.unit_integrand(sec, K)
+        fn0 = sp.lambdify([t1], e, "mpmath")
+
+        def fn(t):
+            # the subtracted integrand cancels like t^2 near 0: evaluate with ample digits
+            with mp.workdps(150):
+                return fn0(t)
+        with mp.workdps(30):
+            v = mp.quad(fn, [0, 1])
+        assert abs(v - c[K + 1]) < 1e-20, (K, v, c[K + 1])
+
+
+@pytest.mark.parametrize("a,b,j", [(0, 1, 0), (-2, 2, 1), (1, -1, 2), (2, -2, 1)])
+def test_direct_expansion_closed_form(a, b, j):
+    """int_0^1 (1+x)^{a+b eps} log(1+x)^j dx = d^j/ds^j (2^{s+1}-1)/(s+1) at s = a + b eps."""
+    prob = W.DirectProblem("t", 1, (0,), (W.DirectFactor(((1.0, (0,)), (1.0, (1,))), a, b),), j, (0, 1, 2))
+    pr = P.direct_problem(prob)
+    got = {K: 0.0 for K in (0, 1, 2)}
+    for u in pr.units:
+        got[u.order] += Q.integrate_box(u.f_numpy, 1)
+    with mp.workdps(30):
+        F = lambda s: (mp.power(2, s + 1) - 1) / (s + 1)
+        g = lambda e: mp.diff(F, a + b * e, j) if j else F(a + b * e)
+        c = mp.taylor(g, 0, 2)
+    for K in (0, 1, 2):
+        assert abs(got[K] - float(c[K])) < 1e-10, (K, got[K], c[K])
+
+
+# ------------------------------------------------------------------ generators
+
+def test_philox_known_answers():
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        ctr, key, out = [[int(w, 16) for w in part.split()] for part in line.split("|")]
+        got = philox4x32_10(*ctr, *key)
+        assert [int(v) for v in got] == out
+
+
+def test_philox_point_layout():
+    U = philox_uniforms(7, 3, 2, (1 << 32) + 5, 3, 5)
+    r = philox4x32_10(np.uint32(5), np.uint32(1), np.uint32(2), np.uint32(2), np.uint32(7), np.uint32(3))
+    m = (int(r[1]) << 20) | (int(r[0]) >> 12)
+    assert U[0, 4] == (2 * m + 1) * 2.0 ** -53
+    assert np.all(U > 0) and np.all(U < 1)
+
+
+def test_sobol_primitive_polynomials_and_first_points():
+    # x+1, x^2+x+1, x^3+x+1, x^3+x^2+1, x^4+x+1, x^4+x^3+1, x^5+x^2+1, x^5+x^3+1
+    assert [p for _, p in primitive_polynomials(8)] == [3, 7, 11, 13, 19, 25, 37, 41]
+    X = sobol_ints(0, 8, 2) / 2.0 ** 32
+    assert X[:, 0].tolist() == [0, .5, .75, .25, .375, .875, .625, .125]
+    assert X[:, 1].tolist() == [0, .5, .25, .75, .375, .875, .125, .625]
+
+
+def test_sobol_net_properties():
+    m = 10
+    X = sobol_ints(0, 1 << m, 8)
+    for j in range(8):                       # (0, m, 1)-net in every coordinate
+        assert len(set((X[:, j] >> (32 - m)).tolist())) == 1 << m
+    for a in range(m + 1):                   # (0, m, 2)-net for coordinates 1 and 2
+        cells = (X[:, 0].astype(np.uint64) >> np.uint64(32 - a)) * (1 << (m - a)) + \
+            (X[:, 1].astype(np.uint64) >> np.uint64(32 - (m - a)))
+        assert len(set(cells.tolist())) == 1 << m
+    U = sobol_uniforms(1, 2, 0, 0, 1 << m, 3)
+    assert np.all(U > 0) and np.all(U < 1)
+
+
+# ----------------------------------------------------------------------- vegas
+
+def test_vegas_linear_function():
+    """The integrator self-test on a linear function; x + 0.2 over [0,1] is 0.7 (Sec. 4.6)."""
+    r = V.integrate_unit(lambda X: X[:, 0] + 0.2, 1, 5, 20000, 11, 0)
+    assert abs(r.value - 0.7) < 4 * r.sigma and r.sigma < 1e-3
+
+
+def test_vegas_map_is_measure_preserving():
+    rng = np.random.default_rng(3)
+    for dim in (1, 3):
+        g = np.sort(rng.uniform(size=(dim, 127)), axis=1)
+        grid = np.concatenate([np.zeros((dim, 1)), g, np.ones((dim, 1))], axis=1)
+        n = 128 * 64
+        u = (np.arange(n) + 0.5) / n
+        X, J, _ = V.vegas_map(grid, np.tile(u[:, None], (1, dim)))
+        for j in range(dim):
+            assert np.all(np.diff(X[:, j]) > 0)
+        # stratified midpoints per bin integrate the constant exactly
+        X1, J1, _ = V.vegas_map(grid[:1], u[:, None])
+        assert abs(J1.mean() - 1.0) < 1e-12
+        # and a linear function exactly (midpoint rule within each linear piece)
+        assert abs(np.mean(J1 * X1[:, 0]) - 0.5) < 1e-12
+
+
+def test_vegas_refine_properties():
+    nb = 128
+    grid = V.uniform_grid(2, nb)
+    same = V.refine(grid, np.ones((2, nb)))
+    assert np.max(np.abs(same - grid)) < 1e-14      # rounding of a 128-term running sum
+    rng = np.random.default_rng(5)
+    h = rng.uniform(size=(2, nb)) ** 4
+    g1 = V.refine(grid, h)
+    g2 = V.refine(grid, 1e6 * h)
+    assert np.max(np.abs(g1 - g2)) < 1e-13
+    assert np.all(np.diff(g1, axis=1) > 0)
+    # equal shares: the piecewise-linear cumulative damped weight at each new edge
+    for j in range(2):
+        d = h[j]
+        s = np.empty(nb)
+        s[0], s[-1] = (d[0] + d[1]) / 2, (d[-2] + d[-1]) / 2
+        s[1:-1] = (d[:-2] + d[1:-1] + d[2:]) / 3
+        r = s / s.sum()
+        w = ((1 - r) / np.log(1 / r)) ** 1.5
+        cum = np.concatenate([[0], np.cumsum(w)])
+        at = np.interp(g1[j], grid[j], cum)
+        assert np.max(np.abs(at - np.arange(nb + 1) * w.sum() / nb)) < 1e-10 * w.sum()
+
+
+def test_vegas_unbiased_over_seeds():
+    pr = P.feynman_problem(W.bubble())
+    u = [x for x in pr.units if x.order == 3][0]
+    exact = Q.integrate_box(u.f_numpy, 1)
+    vals = [V.integrate_unit(u.f_numpy, 1, 3, 4000, seed, 0).value for seed in range(32)]
+    sig = np.std(vals) / math.sqrt(len(vals))
+    assert abs(np.mean(vals) - exact) < 4 * sig
+
+
+def test_error_combination_mean_square():
+    """Sec. 4.3: sector errors are summed in the mean-square norm."""
+    pr = P.feynman_problem(W.bubble())
+    n = len(pr.units)
+    val, err = P.sum_orders(pr, [1.0] * n, [0.3] * n)
+    for K in pr.int_orders:
+        k = sum(1 for u in pr.units if u.order == K)
+        assert abs(err[K] - 0.3 * math.sqrt(k)) < 1e-15 and val[K] == k
