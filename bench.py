@@ -1,0 +1,378 @@
+"""Throughput benchmark of the sector-integrand Monte-Carlo hot path.
+
+One step = one pass of the whole hot path over one workload: every unit
+(sector, eps order) of the one-loop massless box at s = -1, t = -2 (orders
+eps^-2..eps^0, 12 sectors of 3 dims, 32 units) integrated with Vegas,
+10 iterations x 10^6 Philox points per unit (10^7 points per sector per
+order), binary64: point generation, Vegas map, bytecode evaluation,
+reduction, grid refinement and the per-order assembly.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the oracle (the
+plain CPU restatement of the method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (points per unit per iteration, iterations, rng)
+    "box": (1_000_000, 10, "philox"),
+    "bubble": (100_000, 10, "philox"),
+    "double_box": (1_000_000, 1, "philox"),
+    "stress": (1 << 20, 1, "sobol"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="box", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--points", type=int, default=0, help="points per unit per iteration (0: workload default)")
+    ap.add_argument("--iters", type=int, default=0, help="Vegas iterations per step (0: workload default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def prepared(workload):
+    import workloads as W
+    from paper_1511_03614_gb300 import prepare_feynman, prepare_direct
+    if workload == "stress":
+        return prepare_direct(W.stress_suite(), "stress")
+    return prepare_feynman(getattr(W, workload)())
+
+
+def dist_setup(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def op_costs(peaks):
+    """FMA-equivalents of each opcode from the measured pipe rates."""
+    fma_rate = peaks[0] * 1e12 / 2.0                 # binary64 FMA per second
+    log_c = fma_rate / (peaks[1] * 1e9)
+    div_c = fma_rate / (peaks[2] * 1e9)
+    return {"LOG": log_c, "DIV": div_c, "INV": div_c}
+
+
+def unit_work(prog, costs, dim, adapt):
+    """(algorithmic flops, FMA-equivalent pipe slots) per point of one unit.
+
+    Flops: ADD SUB MUL NEG ADDC MULC = 1, MAC MACC = 2, POWI = its multiplies,
+    DIV INV LOG = 1; plus the Vegas map (4 per coordinate: scale, edge difference,
+    interpolation FMA, Jacobian product) and the accumulation (v = f J, v^2, two
+    sums: 4).  Pipe slots weigh LOG/DIV/INV by their measured cost.
+    """
+    c = prog.counts
+    flops = prog.flops()
+    powi = 0
+    for w in prog.code.tolist():
+        if (w & 0xFF) == 12:
+            e = (w >> 24) & 0xFF
+            e = e - 256 if e >= 128 else e
+            m = abs(e)
+            powi += max(m.bit_length() - 1 + bin(m).count("1") - 1, 0) + (1 if e < 0 else 0)
+    flops += powi + c.get("DIV", 0) + c.get("INV", 0) + c.get("LOG", 0)
+    slots = prog.flops() / 1.0 - (c.get("MAC", 0) + c.get("MACC", 0)) + powi + \
+        sum(costs[k] * c.get(k, 0) for k in ("LOG", "DIV", "INV"))
+    extra = 4 * dim + 4
+    return flops + extra, slots + extra
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1511_03614_gb300 import Integrator, _native as N
+    import ctypes as C
+
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    pts, iters, rng = WORKLOADS[args.workload]
+    pts = args.points or pts
+    iters = args.iters or iters
+    prep = prepared(args.workload)
+    lib = N.load()
+    peaks = (C.c_double * 6)()
+    N.check(lib.fiesta_probe_peaks(peaks, 6))
+    peaks = list(peaks)
+    integ = Integrator(prep)
+    kw = dict(n_iter=iters, points=pts, seed=1, rng=rng, precision=args.precision)
+    for _ in range(args.warmup):
+        integ.integrate(**kw)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2
+    clocks = Clocks(local)
+    stream = integ.stream
+    times, eval_ms, launches, eval_launches, points = [], 0.0, 0, 0, 0
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    res = None
+    for s in range(args.steps):
+        flush.fill_(float(s))                          # evict L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = integ.integrate(**kw)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        eval_ms += res.stats["eval_ms"]
+        launches += res.stats["kernels_launched"]
+        eval_launches += res.stats["eval_launches"]
+        points += res.stats["points"]
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop()
+    total_ms = sum(times)
+    t_max = max_over_ranks(total_ms, world)
+    all_points = sum_over_ranks(points, world)
+    value = all_points / (t_max * 1e-3)
+
+    # roofline of the evaluation kernel (dominant): algorithmic work per launch
+    costs = op_costs(peaks)
+    per_unit = [unit_work(u.program, costs, u.dim, True) for u in prep.units]
+    flops_per_launch = sum(f for f, _ in per_unit) * pts
+    slots_per_launch = sum(s for _, s in per_unit) * pts
+    avg_eval_s = eval_ms / max(eval_launches, 1) * 1e-3
+    if args.precision == "fp64":
+        achieved = 2.0 * slots_per_launch / avg_eval_s * 1e-12      # FMA-equivalent TFLOP/s
+        peak_meas = peaks[0]
+        nominal = 1.25
+    else:
+        achieved = 2.0 * slots_per_launch / avg_eval_s * 1e-12
+        peak_meas = peaks[3]
+        nominal = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "TFLOP/s",
+                "frac": achieved / peak_meas, "traffic": None,
+                "kernel": "k_eval", "work": "FMA-equivalent pipe slots x 2 per launch (log/div weighted by "
+                "measured cost)", "peak_source": "measured in-process (fiesta_probe_peaks)",
+                "nominal_fp64_tflops": nominal,
+                "algorithmic_tflops": flops_per_launch / avg_eval_s * 1e-12,
+                "eval_ms_per_launch": avg_eval_s * 1e3,
+                "peaks_measured": {"fp64_tflops": peaks[0], "fp64_log_gps": peaks[1], "fp64_div_gps": peaks[2],
+                                   "fp32_tflops": peaks[3], "fp32_log_gps": peaks[4], "fp32_div_gps": peaks[5]}}
+
+    # end to end through the public API with host buffers: upload programs, integrate,
+    # read the per-order results back; the copies are inside the timed region.
+    e2e = None
+    if not args.no_e2e:
+        h2d = sum(u.program.code.nbytes + u.program.consts.nbytes for u in prep.units) + 64 * len(prep.units)
+        d2h = 16 * len(prep.units) * iters + 8 * len(prep.units)
+        e_times = []
+        e_points = 0
+        for s in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ig = Integrator(prep)
+            r = ig.integrate(**kw)
+            _ = [r.assembled[n] for n in r.assembled] if r.assembled else None
+            ig.close()
+            torch.cuda.synchronize()
+            e_times.append(time.perf_counter() - t0)
+            e_points += r.stats["points"]
+        et = max_over_ranks(sum(e_times), world)
+        e2e = {"value": sum_over_ranks(e_points, world) / et, "unit": "points/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(prep, args.workload, 12.0)
+
+    if rank == 0:
+        line = {
+            "metric": "sampling points/s", "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32 body / f64 map+sums",
+            "data": "synthetic",
+            "config": {"workload": {"box": "one-loop massless box s=-1 t=-2, eps^-2..eps^0, 12 sectors x 3 dims "
+                                           "(32 units), Vegas 10 it x 1e6 Philox points per unit",
+                                    "bubble": "one-loop massless bubble p^2=-1 to eps^2, 8 units, 10 x 1e5",
+                                    "double_box": "planar double box s=t=-1, eps^-4..eps^0, 293 sectors x 6 dims",
+                                    "stress": "10000 seeded synthetic integrands, dims 3..8, 2^20 Sobol points"
+                                    }[args.workload],
+                       "units": len(prep.units), "points_per_unit_per_iter": pts, "iterations": iters,
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": ck,
+            "results": {str(n): [res.assembled[n], res.assembled_errors[n]] for n in res.assembled}
+            if res and res.assembled else None,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(prep_unused, workload, budget_s):
+    """The oracle as it stands, on a bounded sample of the workload, on this host's cores."""
+    import numpy as np
+    import workloads as W
+    from oracle import pipeline as P, vegas as V
+    if workload == "stress":
+        probs = W.stress_suite(200)
+        units = [P.direct_problem(p).units[0] for p in probs]
+    else:
+        units = P.feynman_problem(getattr(W, workload)()).units
+    n = 20000
+    done = 0
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < budget_s and k < 10 * len(units):
+        u = units[k % len(units)]
+        V.integrate_unit(u.f_numpy, u.dim, 1, n, 1, k % len(units), rng="philox" if workload != "stress" else "sobol")
+        done += n
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} unit-iterations x {n} points of the {workload} units (numpy float64, one thread)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as W
+    from oracle import pipeline as P, vegas as V
+    pts, iters, rng = WORKLOADS[args.workload]
+    if args.workload == "stress":
+        units = [P.direct_problem(p).units[0] for p in W.stress_suite(100)]
+    else:
+        units = P.feynman_problem(getattr(W, args.workload)()).units
+    n = 20000
+    for _ in range(args.warmup):
+        V.integrate_unit(units[0].f_numpy, units[0].dim, 1, 2000, 1, 0, rng=rng)
+    times = []
+    done = 0
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        for k, u in enumerate(units[:32]):
+            V.integrate_unit(u.f_numpy, u.dim, 1, n, 1 + s, k, rng=rng)
+            done += n
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = done / total
+    line = {"impl": "reference", "metric": "sampling points/s", "value": value, "unit": "points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": f"{min(32, len(units))} units x {n} points per step"},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{min(32, len(units))} units x {n} Philox/Sobol points per step, one Vegas "
+                                       "iteration each (numpy float64)"},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * fiesta.h -- C ABI of the GB300 sector-integrand Monte-Carlo library.
+ *
+ * The library integrates sector-decomposed, eps-expanded Feynman-parameter
+ * integrands (the "units": one sector at one power of eps) with the VEGAS
+ * algorithm on one GPU.  It is the device half of the method of A. V. Smirnov,
+ * "FIESTA 4: optimized Feynman integral calculations with GPU support"
+ * (arXiv:1511.03614): Sec. 2.1-2.2 describe evaluating each integrand as a
+ * loop over (operator, operand, operand, result) quadruples at batches of
+ * sampling points on the GPU; Sec. 4.4 names Vegas the default integrator;
+ * Sec. 4.3 reports per eps order a value and an error estimate, the errors of
+ * the separately integrated pieces summed in the mean-square norm.
+ *
+ * Conventions for every entry point:
+ *  - Plain C types only.  All arrays are owned by the caller unless stated.
+ *  - A return value of 0 (FIESTA_OK) means success; a negative value is one of
+ *    the FIESTA_E_* codes below and fiesta_last_error() returns a message
+ *    (thread-local, valid until the next call on the same thread).
+ *  - Nothing is computed on the host: if no usable GPU is present every entry
+ *    point that would compute returns FIESTA_E_CUDA.
+ */
+#ifndef FIESTA_H
+#define FIESTA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FIESTA_OK            0
+#define FIESTA_E_INVALID    -1  /* bad argument or program rejected by the validator */
+#define FIESTA_E_NOMEM      -2  /* device memory or shared memory budget exceeded */
+#define FIESTA_E_CUDA       -3  /* CUDA runtime error (message has the CUDA text) */
+#define FIESTA_E_TIMEOUT    -4  /* device time budget expired; the kernel stopped cleanly */
+#define FIESTA_E_NONFINITE  -5  /* a unit produced non-finite samples (unit id in the message) */
+
+#define FIESTA_RNG_PHILOX    0
+#define FIESTA_RNG_SOBOL     1
+#define FIESTA_FP64          0  /* all arithmetic in binary64 */
+#define FIESTA_FP32          1  /* integrand body in binary32; map, Jacobian, sums and grid in binary64 */
+
+#define FIESTA_NBINS       128  /* Vegas bins per coordinate */
+#define FIESTA_MAX_DIM       8  /* largest integration dimension */
+
+/*
+ * One unit: a straight-line register program (the paper's quadruple list,
+ * Sec. 2.1) plus its constants.  Instruction word: op | dst<<8 | a<<16 | b<<24,
+ * opcodes 1..15 as documented in the Python package's bytecode module
+ * (LDX LDC ADD SUB MUL DIV NEG MAC ADDC MULC MACC POWI LOG INV MOV).
+ * code/consts are host pointers, read during fiesta_load_sectors only.
+ */
+typedef struct {
+    int32_t dim;          /* integration dimension, 1..FIESTA_MAX_DIM */
+    int32_t n_instr;      /* number of instruction words, >= 1 */
+    int32_t n_const;      /* number of constants, >= 0 */
+    int32_t n_slots;      /* register-file size, 1..255 */
+    int32_t out_slot;     /* slot holding the integrand value at the end */
+    int32_t order;        /* power of eps of this unit (used for the per-order sums) */
+    int32_t sector;       /* sector number (informational) */
+    uint32_t rng_key;     /* second Philox key word: the unit's point stream */
+    const uint32_t *code; /* n_instr words */
+    const double *consts; /* n_const values */
+} fiesta_program;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  NULL
+ * members select cudaMalloc/cudaFree. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} fiesta_alloc;
+
+typedef struct {
+    int32_t rng;              /* FIESTA_RNG_PHILOX or FIESTA_RNG_SOBOL */
+    int32_t precision;        /* FIESTA_FP64 or FIESTA_FP32 */
+    int32_t n_iter;           /* Vegas iterations, >= 1 */
+    int32_t adapt;            /* nonzero: refine each unit's grid between iterations */
+    int64_t points_per_iter;  /* sampling points per unit per iteration, >= 2 */
+    uint64_t seed;            /* first Philox key word is seed mod 2^32 */
+    double alpha;             /* grid damping exponent (1.5) */
+    int32_t skip_first;       /* nonzero: leave iteration 0 out of the weighted mean */
+    int32_t order_lo;         /* value[k], error[k] refer to eps^(order_lo + k) */
+    int64_t unit_begin;       /* integrate units [unit_begin, unit_end) only ... */
+    int64_t unit_end;         /* ... unit_end <= 0 means all units */
+    int64_t timeout_ms;       /* device time budget per kernel launch; 0 = none */
+    int32_t threads;          /* threads per block; 0 = automatic */
+    int32_t reset_grid;       /* nonzero: start from the uniform grid (else keep the last one) */
+    int32_t iter_offset;      /* added to the iteration number in the point streams */
+    int32_t reserved[5];
+} fiesta_options;
+
+typedef struct {
+    double value;             /* inverse-variance weighted mean over iterations */
+    double sigma;             /* its standard error */
+    double chi2_dof;          /* chi^2 per degree of freedom of the iterations */
+    int64_t n_points;         /* points evaluated for this unit */
+    int32_t order, sector;
+    int64_t n_nonfinite;      /* samples whose value was not finite (counted as 0) */
+} fiesta_unit_result;
+
+typedef struct {
+    double gpu_ms;            /* device time of all launches (CUDA events) */
+    double eval_ms;           /* device time of the evaluation kernel alone */
+    int64_t points;           /* sampling points evaluated */
+    double points_per_s;      /* points / (gpu_ms / 1000) */
+    int32_t kernels_launched; /* kernel launches made by this call */
+    int32_t eval_launches;    /* of which evaluation-kernel launches */
+} fiesta_stats;
+
+typedef struct fiesta_ctx fiesta_ctx;
+
+/*
+ * Copy n_units programs to the device and validate them (opcodes, slot,
+ * coordinate and constant indices, read-before-write).  *out receives a new
+ * context, owned by the caller and released by fiesta_free.  cuda_stream is a
+ * cudaStream_t (NULL: the default stream) on which every later call runs.
+ * Errors: FIESTA_E_INVALID (a program is rejected, index in the message),
+ * FIESTA_E_NOMEM, FIESTA_E_CUDA.
+ */
+int fiesta_load_sectors(fiesta_ctx **out, const fiesta_program *progs, int64_t n_units,
+                        const fiesta_alloc *alloc, void *cuda_stream);
+
+/*
+ * Integrate every unit of the slice with Vegas (Sec. 4.4) and return, per eps
+ * order order_lo + k (k < n_orders), the sum over units of that order in
+ * value[k] and the mean-square combination sqrt(sum sigma^2) of their errors
+ * in error[k] (Sec. 4.3).  value/error are caller-owned host arrays of
+ * n_orders doubles.  per_unit (nullable) receives one record per unit of the
+ * slice, in unit order; stats (nullable) the timing.  The grids persist in the
+ * context between calls (see reset_grid).
+ * Errors: FIESTA_E_INVALID, FIESTA_E_CUDA, FIESTA_E_TIMEOUT, FIESTA_E_NONFINITE
+ * (results are still written; the message names the first unit affected).
+ */
+int fiesta_integrate(fiesta_ctx *ctx, const fiesta_options *opt, double *value, double *error,
+                     int32_t n_orders, fiesta_unit_result *per_unit, fiesta_stats *stats);
+
+/*
+ * Evaluate unit `unit` at n points: x is n*dim coordinates in (0,1), row-major,
+ * f receives n values.  x and f are both host or both device pointers (the
+ * library detects which).  precision is FIESTA_FP64 or FIESTA_FP32.  This is
+ * the per-point hook, the counterpart of the paper's justEvaluate integrator
+ * (Sec. 4.4).  Errors: FIESTA_E_INVALID, FIESTA_E_CUDA.
+ */
+int fiesta_eval_batch(fiesta_ctx *ctx, int64_t unit, int32_t precision, const double *x, int64_t n,
+                      double *f);
+
+/*
+ * Per-iteration results of the last fiesta_integrate call for one unit:
+ * mean[i] and var[i] (variance of the mean) for i < n_iter, host arrays.
+ */
+int fiesta_iterations(fiesta_ctx *ctx, int64_t unit, int32_t n_iter, double *mean, double *var);
+
+/* Copy one unit's Vegas grid (dim * (FIESTA_NBINS+1) edges, row per coordinate)
+ * to the host array `grid`, or set it from `grid` (checkpoint and resume). */
+int fiesta_get_grid(fiesta_ctx *ctx, int64_t unit, double *grid);
+int fiesta_set_grid(fiesta_ctx *ctx, int64_t unit, const double *grid);
+
+/* Apply one Vegas refinement (smoothing, damping, re-binning) to `n` grids
+ * of dimension `dim` from their v^2 histograms, on the device: grid is
+ * n*dim*(NB+1) edges, hist n*dim*NB sums, both host arrays; grid is updated
+ * in place.  Exposed so the refinement step can be checked on its own. */
+int fiesta_refine(fiesta_ctx *ctx, int32_t dim, int64_t n, double alpha, double *grid, const double *hist);
+
+/*
+ * Measurement support (no counterpart in the paper): measured throughput of
+ * the arithmetic pipes on the current device, used to turn an integrand's
+ * instruction mix into a lower bound on its evaluation time.  out (host, >= 6
+ * doubles): [0] binary64 FMA TFLOP/s, [1] binary64 log G/s, [2] binary64
+ * divide G/s, [3] binary32 FMA TFLOP/s, [4] binary32 logf G/s, [5] binary32
+ * divide G/s.  Allocates and frees a small scratch buffer.
+ */
+int fiesta_probe_peaks(double *out, int32_t n);
+
+void fiesta_free(fiesta_ctx *ctx);
+const char *fiesta_last_error(void);
+int fiesta_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIESTA_H */

@@ -120,3 +120,35 @@ def assemble(prob, val, err):
                 s += float(c) ** 2 * err[K] ** 2
         E[n] = math.sqrt(s)
     return {n: float(v) for n, v in R.items()}, E
+
+
+def _absify(e):
+    """Sum of absolute values of the additive terms at every level of the expression.
+
+    |f_computed - f| <= c u M(x) bounds the rounding error of any evaluation
+    order of f (u the unit roundoff, c of the order of the operation count);
+    M is the condition-scaled magnitude used for per-point tolerances where the
+    subtraction differences cancel.
+    """
+    if e.is_Add:
+        return sp.Add(*[_absify(a) for a in e.args])
+    if e.is_Mul:
+        return sp.Mul(*[_absify(a) for a in e.args])
+    if e.is_Pow:
+        b, x = e.args
+        return sp.Pow(_absify(b), x)
+    if isinstance(e, sp.log):
+        return sp.Abs(e) + 1
+    if e.is_Number:
+        return sp.Abs(e)
+    return sp.Abs(e)
+
+
+def magnitude_numpy(unit, X):
+    """M(x) of ``_absify`` at points X (n, dim), float64."""
+    if getattr(unit, "_abs", None) is None:
+        syms = [S.tsym(j) for j in unit.variables]
+        unit._abs = sp.lambdify(syms, _absify(unit.expr), modules="numpy")
+    with np.errstate(all="ignore"):
+        v = unit._abs(*[X[:, i] for i in range(unit.dim)])
+    return np.broadcast_to(np.asarray(v, dtype=np.float64), (X.shape[0],)).copy()

@@ -1,0 +1,98 @@
+"""ctypes declarations of the C ABI in include/fiesta.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB
+
+FIESTA_OK = 0
+ERRORS = {-1: "FIESTA_E_INVALID", -2: "FIESTA_E_NOMEM", -3: "FIESTA_E_CUDA",
+          -4: "FIESTA_E_TIMEOUT", -5: "FIESTA_E_NONFINITE"}
+RNG = {"philox": 0, "sobol": 1}
+PRECISION = {"fp64": 0, "fp32": 1}
+NBINS = 128
+MAX_DIM = 8
+
+
+class Program(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_instr", C.c_int32), ("n_const", C.c_int32), ("n_slots", C.c_int32),
+                ("out_slot", C.c_int32), ("order", C.c_int32), ("sector", C.c_int32), ("rng_key", C.c_uint32),
+                ("code", C.POINTER(C.c_uint32)), ("consts", C.POINTER(C.c_double))]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Alloc(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("rng", C.c_int32), ("precision", C.c_int32), ("n_iter", C.c_int32), ("adapt", C.c_int32),
+                ("points_per_iter", C.c_int64), ("seed", C.c_uint64), ("alpha", C.c_double),
+                ("skip_first", C.c_int32), ("order_lo", C.c_int32), ("unit_begin", C.c_int64),
+                ("unit_end", C.c_int64), ("timeout_ms", C.c_int64), ("threads", C.c_int32),
+                ("reset_grid", C.c_int32), ("iter_offset", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+class UnitResult(C.Structure):
+    _fields_ = [("value", C.c_double), ("sigma", C.c_double), ("chi2_dof", C.c_double), ("n_points", C.c_int64),
+                ("order", C.c_int32), ("sector", C.c_int32), ("n_nonfinite", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("gpu_ms", C.c_double), ("eval_ms", C.c_double), ("points", C.c_int64),
+                ("points_per_s", C.c_double), ("kernels_launched", C.c_int32), ("eval_launches", C.c_int32)]
+
+
+EXPORTS = {
+    "fiesta_load_sectors": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Program), C.c_int64, C.POINTER(Alloc),
+                                      C.c_void_p]),
+    "fiesta_integrate": (C.c_int, [C.c_void_p, C.POINTER(Options), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.c_int32, C.POINTER(UnitResult), C.POINTER(Stats)]),
+    "fiesta_eval_batch": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]),
+    "fiesta_iterations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
+    "fiesta_get_grid": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "fiesta_set_grid": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "fiesta_refine": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.POINTER(C.c_double),
+                                C.POINTER(C.c_double)]),
+    "fiesta_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.c_int32]),
+    "fiesta_free": (None, [C.c_void_p]),
+    "fiesta_last_error": (C.c_char_p, []),
+    "fiesta_version": (C.c_int, []),
+}
+
+_lib = None
+
+
+class FiestaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path=None):
+    """Load the compiled library; raises if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() "
+                           "(or python -m paper_1511_03614_gb300.build) on a machine with nvcc")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(code):
+    if code != FIESTA_OK:
+        msg = _lib.fiesta_last_error().decode(errors="replace") if _lib else ""
+        raise FiestaError(code, msg)

@@ -1,0 +1,156 @@
+"""Python binding of the C ABI: argument marshalling only.
+
+Every step of the integration runs in the CUDA library; PyTorch provides the
+device, the stream and (through allocator callbacks) the device memory.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+
+from . import _native as N
+from .preprocess import assemble
+
+
+@dataclasses.dataclass
+class Result:
+    values: dict              # eps order -> sum over units of that order
+    errors: dict              # eps order -> mean-square combined error
+    per_unit: list            # dicts: value, sigma, chi2_dof, n_points, order, sector, n_nonfinite
+    stats: dict
+    assembled: dict = None    # eps order -> value with the prefactor series multiplied in
+    assembled_errors: dict = None
+
+
+class Integrator:
+    """Holds the device copy of a Prepared set of units (one fiesta_ctx)."""
+
+    def __init__(self, prep, device=None, stream=None, torch_alloc=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: the integrator has no CPU path")
+        self.lib = N.load()
+        self.prep = prep
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._torch = torch
+        self._bufs = {}
+        n = len(prep.units)
+        progs = (N.Program * n)()
+        keep = []
+        for i, u in enumerate(prep.units):
+            code = np.ascontiguousarray(u.program.code, dtype=np.uint32)
+            cons = np.ascontiguousarray(u.program.consts, dtype=np.float64)
+            if cons.size == 0:
+                cons = np.zeros(1)
+            keep += [code, cons]
+            progs[i] = N.Program(u.dim, code.size, len(u.program.consts), u.program.n_slots, u.program.out_slot,
+                                 u.order, u.sector, u.rng_key & 0xFFFFFFFF,
+                                 code.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                 cons.ctypes.data_as(C.POINTER(C.c_double)))
+        alloc = None
+        if torch_alloc:
+            dev = self.device
+
+            def _alloc(nbytes, user):
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+                self._bufs[t.data_ptr()] = t
+                return t.data_ptr()
+
+            def _free(ptr, user):
+                self._bufs.pop(ptr, None)
+            self._alloc_cb = N.ALLOC_FN(_alloc)
+            self._free_cb = N.FREE_FN(_free)
+            alloc = N.Alloc(self._alloc_cb, self._free_cb, None)
+        ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(self.lib.fiesta_load_sectors(C.byref(ctx), progs, n, C.byref(alloc) if alloc else None,
+                                                 C.c_void_p(self.stream.cuda_stream)))
+        self.ctx = ctx
+        del keep
+
+    # ------------------------------------------------------------------ integrate
+    def integrate(self, n_iter=10, points=100_000, seed=1, rng="philox", precision="fp64", adapt=True,
+                  alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
+                  iter_offset=0, assemble_result=True, raise_nonfinite=True):
+        orders = [u.order for u in self.prep.units]
+        lo, hi = min(orders), max(orders)
+        nord = hi - lo + 1
+        b, e = (0, len(self.prep.units)) if units is None else units
+        opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(bool(adapt)), int(points),
+                        int(seed) & 0xFFFFFFFFFFFFFFFF, float(alpha), int(bool(skip_first)), lo, int(b), int(e),
+                        int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset))
+        val = (C.c_double * nord)()
+        err = (C.c_double * nord)()
+        per = (N.UnitResult * (e - b))()
+        st = N.Stats()
+        with self._torch.cuda.device(self.device):
+            rc = self.lib.fiesta_integrate(self.ctx, C.byref(opt), val, err, nord, per, C.byref(st))
+        if rc != N.FIESTA_OK and not (rc == -5 and not raise_nonfinite):
+            N.check(rc)
+        values = {lo + k: val[k] for k in range(nord)}
+        errors = {lo + k: err[k] for k in range(nord)}
+        pu = [dict(value=r.value, sigma=r.sigma, chi2_dof=r.chi2_dof, n_points=r.n_points, order=r.order,
+                   sector=r.sector, n_nonfinite=r.n_nonfinite) for r in per]
+        stats = dict(gpu_ms=st.gpu_ms, eval_ms=st.eval_ms, points=st.points, points_per_s=st.points_per_s,
+                     kernels_launched=st.kernels_launched, eval_launches=st.eval_launches)
+        res = Result(values, errors, pu, stats)
+        if assemble_result and units is None:
+            res.assembled, res.assembled_errors = assemble(self.prep, values, errors)
+        return res
+
+    # ------------------------------------------------------------------ per point
+    def eval_batch(self, unit, x, precision="fp64"):
+        """f at points x (n, dim): a torch CUDA tensor (result on the device) or a host array."""
+        torch = self._torch
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            x = x.to(torch.float64).contiguous()
+            f = torch.empty(x.shape[0], dtype=torch.float64, device=x.device)
+            with torch.cuda.device(self.device):
+                N.check(self.lib.fiesta_eval_batch(self.ctx, int(unit), N.PRECISION[precision],
+                                                   C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(f.data_ptr())))
+            return f
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        f = np.empty(x.shape[0])
+        with torch.cuda.device(self.device):
+            N.check(self.lib.fiesta_eval_batch(self.ctx, int(unit), N.PRECISION[precision],
+                                               x.ctypes.data_as(C.c_void_p), x.shape[0], f.ctypes.data_as(C.c_void_p)))
+        return f
+
+    def iterations(self, unit, n_iter):
+        m = (C.c_double * n_iter)()
+        v = (C.c_double * n_iter)()
+        N.check(self.lib.fiesta_iterations(self.ctx, int(unit), int(n_iter), m, v))
+        return np.array(m[:]), np.array(v[:])
+
+    def get_grid(self, unit):
+        d = self.prep.units[unit].dim
+        g = np.empty(d * (N.NBINS + 1))
+        N.check(self.lib.fiesta_get_grid(self.ctx, int(unit), g.ctypes.data_as(C.POINTER(C.c_double))))
+        return g.reshape(d, N.NBINS + 1)
+
+    def set_grid(self, unit, grid):
+        g = np.ascontiguousarray(grid, dtype=np.float64).ravel()
+        N.check(self.lib.fiesta_set_grid(self.ctx, int(unit), g.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def refine(self, grids, hists, alpha=1.5):
+        """Device refinement of grids (n, dim, NB+1) from histograms (n, dim, NB); returns new grids."""
+        g = np.ascontiguousarray(grids, dtype=np.float64).copy()
+        h = np.ascontiguousarray(hists, dtype=np.float64)
+        n, dim = g.shape[0], g.shape[1]
+        N.check(self.lib.fiesta_refine(self.ctx, dim, n, float(alpha), g.ctypes.data_as(C.POINTER(C.c_double)),
+                                       h.ctypes.data_as(C.POINTER(C.c_double))))
+        return g
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.fiesta_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,261 @@
+"""Register bytecode: the straight-line program the device interpreter runs.
+
+Each instruction is one 32-bit word ``op | dst << 8 | a << 16 | b << 24`` over a
+per-thread file of at most 255 slots, plus a per-program pool of binary64
+constants (the coefficients of the polynomials and of the eps expansion).
+This is the project's form of the paper's quadruple list (Sec. 2.1).
+
+Opcodes (slot[i] is written s[i], c[k] a constant, x[j] a coordinate):
+
+====  =====  =========================================
+ 1    LDX    s[d] = x[a]
+ 2    LDC    s[d] = c[a | b << 8]
+ 3    ADD    s[d] = s[a] + s[b]
+ 4    SUB    s[d] = s[a] - s[b]
+ 5    MUL    s[d] = s[a] * s[b]
+ 6    DIV    s[d] = s[a] / s[b]
+ 7    NEG    s[d] = -s[a]
+ 8    MAC    s[d] = s[a] * s[b] + s[d]
+ 9    ADDC   s[d] = s[a] + c[b]
+10    MULC   s[d] = s[a] * c[b]
+11    MACC   s[d] = s[a] * c[b] + s[d]
+12    POWI   s[d] = s[a] ** n,  n = b as a signed byte
+13    LOG    s[d] = log(s[a])
+14    INV    s[d] = 1 / s[a]
+15    MOV    s[d] = s[a]
+====  =====  =========================================
+
+An instruction reads its operands before it writes s[d], so d may equal a or b.
+The result of the program is s[out_slot].
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+OPS = {"LDX": 1, "LDC": 2, "ADD": 3, "SUB": 4, "MUL": 5, "DIV": 6, "NEG": 7, "MAC": 8,
+       "ADDC": 9, "MULC": 10, "MACC": 11, "POWI": 12, "LOG": 13, "INV": 14, "MOV": 15}
+NAMES = {v: k for k, v in OPS.items()}
+MAX_SLOTS = 255
+MAX_CONST = 65536
+
+
+def encode(op, d=0, a=0, b=0):
+    return (OPS[op] & 0xFF) | (d & 0xFF) << 8 | (a & 0xFF) << 16 | (b & 0xFF) << 24
+
+
+def decode(word):
+    return word & 0xFF, (word >> 8) & 0xFF, (word >> 16) & 0xFF, (word >> 24) & 0xFF
+
+
+@dataclasses.dataclass
+class Program:
+    code: np.ndarray        # uint32
+    consts: np.ndarray      # float64
+    n_slots: int
+    out_slot: int
+    dim: int
+    counts: dict            # opcode name -> number of instructions
+
+    def flops(self):
+        """Arithmetic operations per point: ADD/SUB/MUL/NEG/ADDC/MULC = 1, MAC/MACC = 2,
+        DIV/INV/LOG/POWI counted separately in ``counts``."""
+        c = self.counts
+        return sum(c.get(k, 0) for k in ("ADD", "SUB", "MUL", "NEG", "ADDC", "MULC")) + \
+            2 * (c.get("MAC", 0) + c.get("MACC", 0))
+
+
+def emit(graph, out, dim):
+    """Lower the nodes reachable from ``out`` to a Program (linear-scan slot allocation)."""
+    nodes = graph.nodes
+    live = set()
+    stack = [out]
+    while stack:
+        i = stack.pop()
+        if i in live:
+            continue
+        live.add(i)
+        n = nodes[i]
+        if n[0] in ("add", "sub", "mul", "div"):
+            stack += [n[1], n[2]]
+        elif n[0] == "fma":
+            stack += [n[1], n[2], n[3]]
+        elif n[0] in ("neg", "log", "inv", "powi"):
+            stack.append(n[1])
+    order = sorted(live)
+
+    consts = []
+    cidx = {}
+
+    def const_index(v):
+        if v not in cidx:
+            cidx[v] = len(consts)
+            consts.append(v)
+        return cidx[v]
+
+    def is_small_const(i):
+        n = nodes[i]
+        if n[0] != "c":
+            return False
+        k = const_index(n[1])
+        return k < 256
+
+    # operands that are folded constants do not need slots
+    folded = set()
+    for i in order:
+        n = nodes[i]
+        if n[0] in ("add", "mul") and (is_small_const(n[1]) or is_small_const(n[2])):
+            folded.add((i, n[1] if is_small_const(n[1]) else n[2]))
+        elif n[0] == "fma" and is_small_const(n[2]):
+            folded.add((i, n[2]))
+    # which node ids are needed in a slot and where they are used last
+    uses = {}
+    for pos, i in enumerate(order):
+        n = nodes[i]
+        args = ()
+        if n[0] in ("add", "sub", "mul", "div"):
+            args = (n[1], n[2])
+        elif n[0] == "fma":
+            args = (n[1], n[2], n[3])
+        elif n[0] in ("neg", "log", "inv", "powi"):
+            args = (n[1],)
+        for a in args:
+            if (i, a) in folded:
+                continue
+            uses.setdefault(a, []).append(pos)
+    last = {a: max(p) for a, p in uses.items()}
+    last[out] = len(order)
+
+    code = []
+    counts = {}
+    slot = {}
+    free = []
+    n_slots = 0
+
+    def put(op, d=0, a=0, b=0):
+        code.append(encode(op, d, a, b))
+        counts[op] = counts.get(op, 0) + 1
+
+    def alloc():
+        nonlocal n_slots
+        if free:
+            return free.pop()
+        n_slots += 1
+        if n_slots > MAX_SLOTS:
+            raise OverflowError("program needs more than 255 slots")
+        return n_slots - 1
+
+    for pos, i in enumerate(order):
+        n = nodes[i]
+        kind = n[0]
+        if kind == "c" and i not in uses and i != out:
+            continue                      # only used folded
+        # release operands whose last use is here (their slots may be reused by dst)
+        args = ()
+        if kind in ("add", "sub", "mul", "div"):
+            args = (n[1], n[2])
+        elif kind == "fma":
+            args = (n[1], n[2], n[3])
+        elif kind in ("neg", "log", "inv", "powi"):
+            args = (n[1],)
+        dying = [a for a in dict.fromkeys(args) if a in slot and last.get(a) == pos]
+        if kind == "fma":
+            acc = n[3]
+            if acc in dying:
+                d = slot[acc]             # accumulate in place
+                for a in dying:
+                    if a != acc:
+                        free.append(slot[a])
+            else:
+                # the copy of the accumulator is written before the multiply reads
+                # its operands, so it must not land in an operand's slot
+                d = alloc()
+                put("MOV", d, slot[acc])
+                for a in dying:
+                    free.append(slot[a])
+            if (i, n[2]) in folded:
+                put("MACC", d, slot[n[1]], const_index(nodes[n[2]][1]))
+            else:
+                put("MAC", d, slot[n[1]], slot[n[2]])
+            slot[i] = d
+            continue
+        for a in dying:
+            free.append(slot[a])
+        d = alloc()
+        slot[i] = d
+        if kind == "x":
+            put("LDX", d, n[1])
+        elif kind == "c":
+            k = const_index(n[1])
+            put("LDC", d, k & 0xFF, k >> 8)
+        elif kind in ("add", "mul"):
+            if (i, n[1]) in folded or (i, n[2]) in folded:
+                cnode, other = (n[1], n[2]) if (i, n[1]) in folded else (n[2], n[1])
+                put("ADDC" if kind == "add" else "MULC", d, slot[other], const_index(nodes[cnode][1]))
+            else:
+                put(kind.upper(), d, slot[n[1]], slot[n[2]])
+        elif kind in ("sub", "div"):
+            put(kind.upper(), d, slot[n[1]], slot[n[2]])
+        elif kind in ("neg", "log", "inv"):
+            put(kind.upper(), d, slot[n[1]])
+        elif kind == "powi":
+            e = n[2]
+            if not -128 <= e <= 127:
+                raise OverflowError("integer power out of range")
+            put("POWI", d, slot[n[1]], e & 0xFF)
+        else:
+            raise ValueError(kind)
+    if len(consts) > MAX_CONST:
+        raise OverflowError("too many constants")
+    prog = Program(np.array(code, dtype=np.uint32), np.array(consts, dtype=np.float64),
+                   max(n_slots, 1), slot[out], dim, counts)
+    validate(prog)
+    return prog
+
+
+def validate(prog):
+    """Host-side check of a program: opcodes, slot, coordinate and constant indices,
+    and that no slot is read before it is written."""
+    written = set()
+    R = prog.n_slots
+    nc = len(prog.consts)
+    if not 1 <= prog.dim <= 8:
+        raise ValueError("dimension must be 1..8")
+    if R > MAX_SLOTS:
+        raise ValueError("too many slots")
+    for pc, w in enumerate(prog.code.tolist()):
+        op, d, a, b = decode(w)
+        name = NAMES.get(op)
+        if name is None:
+            raise ValueError(f"bad opcode {op} at {pc}")
+        reads = []
+        if name == "LDX":
+            if a >= prog.dim:
+                raise ValueError(f"coordinate {a} out of range at {pc}")
+        elif name == "LDC":
+            if (a | b << 8) >= nc:
+                raise ValueError(f"constant out of range at {pc}")
+        elif name in ("ADD", "SUB", "MUL", "DIV"):
+            reads = [a, b]
+        elif name == "MAC":
+            reads = [a, b, d]
+        elif name in ("ADDC", "MULC"):
+            reads = [a]
+            if b >= nc:
+                raise ValueError(f"constant out of range at {pc}")
+        elif name == "MACC":
+            reads = [a, d]
+            if b >= nc:
+                raise ValueError(f"constant out of range at {pc}")
+        elif name in ("NEG", "LOG", "INV", "MOV", "POWI"):
+            reads = [a]
+        for r in reads + [d]:
+            if r >= R:
+                raise ValueError(f"slot {r} out of range at {pc}")
+        for r in reads:
+            if r not in written:
+                raise ValueError(f"slot {r} read before written at {pc}")
+        written.add(d)
+    if prog.out_slot not in written:
+        raise ValueError("output slot never written")

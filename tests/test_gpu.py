@@ -1,0 +1,225 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the oracle."""
+import math
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import pipeline as P, vegas as V, quadrature as Q
+
+from gpu_common import need_gpu, feynman, integrator, stress, test_points
+
+pytestmark = pytest.mark.gpu
+
+# Tolerances.  Per point: relative 1e-12 (binary64) / 1e-5 (binary32 body) against
+# a 50-digit evaluation of the oracle's expression where all coordinates are at
+# least 1/16 away from 0; everywhere, |f_gpu - f| <= tol * M(x) with M the
+# oracle's condition-scaled magnitude (sum of absolute values of the additive
+# terms), which bounds the rounding error of any order of evaluation.
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def _ref(unit, X):
+    with mp.workdps(50):
+        return np.array([float(unit.f_mp(x, 50)) for x in X])
+
+
+def _check_points(prep, orc, idx, precision, rng):
+    integ = integrator_for(prep)
+    worst_strict = 0.0
+    for i in idx:
+        u, o = prep.units[i], orc.units[i]
+        X = test_points(u.dim, rng, 48)
+        f = integ.eval_batch(i, X, precision)
+        ref = _ref(o, X)
+        M = P.magnitude_numpy(o, X)
+        tol = TOL[precision]
+        assert np.all(np.abs(f - ref) <= tol * np.maximum(M, 1e-300)), (i, np.max(np.abs(f - ref) / M))
+        inner = np.all(X >= 1.0 / 16, axis=1) & (np.abs(ref) > 1e-3 * M)
+        if inner.any():
+            rel = np.abs(f[inner] - ref[inner]) / np.abs(ref[inner])
+            worst_strict = max(worst_strict, float(rel.max()))
+            assert rel.max() <= tol, (i, rel.max())
+    return worst_strict
+
+
+_INTEG = {}
+
+
+def integrator_for(prep):
+    from paper_1511_03614_gb300 import Integrator
+    key = id(prep)
+    if key not in _INTEG:
+        _INTEG[key] = Integrator(prep)
+    return _INTEG[key]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["bubble", "box"])
+def test_eval_batch_parity_all_units(name, precision):
+    need_gpu()
+    prep, orc = feynman(name)
+    _check_points(prep, orc, range(len(prep.units)), precision, np.random.default_rng(10))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_eval_batch_parity_double_box_sample(precision):
+    need_gpu()
+    prep, orc = feynman("double_box")
+    rng = np.random.default_rng(11)
+    idx = rng.choice(len(prep.units), 12, replace=False)
+    _check_points(prep, orc, idx, precision, rng)
+
+
+def test_eval_batch_device_pointers():
+    torch = need_gpu()
+    prep, orc = feynman("box")
+    integ = integrator("box")
+    rng = np.random.default_rng(12)
+    X = rng.uniform(size=(1000, 3))
+    f_host = integ.eval_batch(5, X)
+    f_dev = integ.eval_batch(5, torch.tensor(X, device="cuda")).cpu().numpy()
+    assert np.array_equal(f_host, f_dev)
+
+
+@pytest.mark.parametrize("name", ["bubble", "box"])
+def test_same_points_first_iteration(name):
+    """Iteration 0 on the uniform grid: GPU sum(v) vs the oracle's on the same Philox points."""
+    need_gpu()
+    prep, orc = feynman(name)
+    integ = integrator(name)
+    N = 20000
+    integ.integrate(n_iter=1, points=N, seed=7, adapt=False)
+    for i, (u, o) in enumerate(zip(prep.units, orc.units)):
+        m, _ = integ.iterations(i, 1)
+        r = V.integrate_unit(o.f_numpy, o.dim, 1, N, 7, u.rng_key, adapt=False)
+        I, var, sv, sv2 = r.iters[0]
+        U = V.philox.uniforms(7, u.rng_key, 0, 0, N, o.dim)
+        X, J, _ = V.vegas_map(r.grids[0], U)
+        absum = np.sum(np.abs(o.f_numpy(X) * J)) / N
+        assert abs(m[0] - I) <= 1e-11 * absum, (i, m[0], I)
+
+
+def test_vegas_iterations_follow_oracle():
+    """Three adapted iterations: means follow the oracle's through the refined grids."""
+    need_gpu()
+    prep, orc = feynman("box")
+    integ = integrator("box")
+    N = 16384
+    integ.integrate(n_iter=3, points=N, seed=3, adapt=True)
+    for i in (0, 5, 17, len(prep.units) - 1):
+        u, o = prep.units[i], orc.units[i]
+        m, _ = integ.iterations(i, 3)
+        r = V.integrate_unit(o.f_numpy, o.dim, 3, N, 3, u.rng_key)
+        for it in range(3):
+            assert abs(m[it] - r.iters[it][0]) <= 1e-9 * (abs(r.iters[it][0]) + math.sqrt(r.iters[it][1])), (i, it)
+        g = integ.get_grid(i)
+        g_or = V.refine(r.grids[1], r.hists[1])
+        assert np.max(np.abs(g - g_or)) < 1e-9
+
+
+def test_refine_parity():
+    need_gpu()
+    integ = integrator("bubble")
+    rng = np.random.default_rng(4)
+    for dim in (1, 3, 8):
+        n = 5
+        grids = np.stack([V.uniform_grid(dim) for _ in range(n)])
+        grids[:, :, 1:-1] = np.sort(rng.uniform(size=(n, dim, 127)), axis=2)
+        hists = rng.uniform(size=(n, dim, 128)) ** 6
+        hists[0, 0, 5:] = 0.0                         # sparse histogram
+        got = integ.refine(grids, hists, 1.5)
+        for k in range(n):
+            ref = V.refine(grids[k], hists[k], 1.5)
+            assert np.max(np.abs(got[k] - ref)) < 1e-12
+
+
+def test_bubble_closed_form():
+    need_gpu()
+    integ = integrator("bubble")
+    res = integ.integrate(n_iter=10, points=100_000, seed=1)
+    z3 = float(mp.zeta(3))
+    exact = {-1: 1.0, 0: 2.0, 1: 4 - math.pi ** 2 / 12, 2: 8 - math.pi ** 2 / 6 - 7 * z3 / 3}
+    for n, v in exact.items():
+        s = res.assembled_errors[n]
+        assert 0 < s < 1e-3
+        assert abs(res.assembled[n] - v) < 4 * s, (n, res.assembled[n], v, s)
+
+
+def test_box_closed_form():
+    need_gpu()
+    integ = integrator("box")
+    res = integ.integrate(n_iter=10, points=1_000_000, seed=2)
+    exact = {-2: 2.0, -1: -math.log(2.0), 0: -2 * math.pi ** 2 / 3}
+    for n, v in exact.items():
+        s = res.assembled_errors[n]
+        assert 0 < s < 2e-3
+        assert abs(res.assembled[n] - v) < 4 * s, (n, res.assembled[n], v, s)
+
+
+def test_fp32_box_within_errors():
+    need_gpu()
+    integ = integrator("box")
+    r64 = integ.integrate(n_iter=6, points=400_000, seed=5, precision="fp64")
+    r32 = integ.integrate(n_iter=6, points=400_000, seed=5, precision="fp32")
+    for n in r64.assembled:
+        s = math.hypot(r64.assembled_errors[n], r32.assembled_errors[n])
+        assert abs(r64.assembled[n] - r32.assembled[n]) < 3 * s + 1e-6
+
+
+def test_linear_text_integrand():
+    """The paper's worker example x[1]+0.2 integrates to 0.7 (Sec. 4.6)."""
+    need_gpu()
+    from paper_1511_03614_gb300 import parse_text, Integrator
+    integ = Integrator(parse_text("1;\n0;\nx[1]+0.2;\n|"))
+    res = integ.integrate(n_iter=5, points=100_000, seed=9)
+    assert abs(res.values[0] - 0.7) < 4 * res.errors[0] and res.errors[0] < 1e-4
+
+
+def test_stress_sobol_same_points():
+    need_gpu()
+    probs, prep, integ = stress(64)
+    N = 4096
+    integ.integrate(n_iter=1, points=N, seed=11, rng="sobol", adapt=False)
+    for k in range(0, 64, 4):
+        orc = P.direct_problem(probs[k])
+        o = orc.units[0]
+        m, _ = integ.iterations(k, 1)
+        r = V.integrate_unit(o.f_numpy, o.dim, 1, N, 11, prep.units[k].rng_key, rng="sobol", adapt=False)
+        U = V.sobol.uniforms(11, prep.units[k].rng_key, 0, 0, N, o.dim)
+        X, J, _ = V.vegas_map(r.grids[0], U)
+        absum = np.mean(np.abs(o.f_numpy(X) * J))
+        assert abs(m[0] - r.iters[0][0]) <= 1e-11 * absum, k
+
+
+def test_deterministic_without_adaptation():
+    need_gpu()
+    integ = integrator("box")
+    a = integ.integrate(n_iter=2, points=50_000, seed=21, adapt=False)
+    b = integ.integrate(n_iter=2, points=50_000, seed=21, adapt=False)
+    assert [u["value"] for u in a.per_unit] == [u["value"] for u in b.per_unit]
+
+
+def test_timeout_returns_cleanly():
+    need_gpu()
+    from paper_1511_03614_gb300._native import FiestaError
+    integ = integrator("box")
+    with pytest.raises(FiestaError) as e:
+        integ.integrate(n_iter=1, points=50_000_000, seed=1, timeout_ms=1)
+    assert e.value.code == -4
+    res = integ.integrate(n_iter=2, points=10_000, seed=1)     # context still usable
+    assert math.isfinite(res.values[0])
+
+
+def test_nonfinite_samples_are_reported():
+    """Fault injection on the host: a NaN constant in one unit's program."""
+    need_gpu()
+    from paper_1511_03614_gb300 import parse_text, Integrator
+    from paper_1511_03614_gb300._native import FiestaError
+    prep = parse_text("1; 0; x[1]*0.5 + 1.0; |")
+    prep.units[0].program.consts[:] = np.nan
+    integ = Integrator(prep)
+    with pytest.raises(FiestaError) as e:
+        integ.integrate(n_iter=1, points=1000)
+    assert e.value.code == -5 and "unit 0" in str(e.value)

@@ -1,0 +1,123 @@
+"""Host-side tests of the product path that need no GPU: the preprocessor
+against the oracle (through a test-only bytecode interpreter), the validator,
+and the C ABI library's exports."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import pipeline as P
+from paper_1511_03614_gb300 import bytecode as B, prepare_feynman, prepare_direct, parse_text
+from paper_1511_03614_gb300 import prefactor as PF
+from oracle.prefactor import prefactor_series
+
+from bytecode_interp import run
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("name", ["bubble", "box"])
+def test_programs_match_oracle_integrands(name):
+    prob = getattr(W, name)()
+    prep = prepare_feynman(prob)
+    orc = P.feynman_problem(prob)
+    assert [(u.sector, u.order) for u in prep.units] == [(u.sector, u.order) for u in orc.units]
+    rng = np.random.default_rng(1)
+    for u, o in zip(prep.units, orc.units):
+        X = rng.uniform(0.05, 1.0, size=(64, u.dim))
+        a, b = run(u.program, X), o.f_numpy(X)
+        assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)) < 1e-12
+
+
+def test_double_box_programs_sample():
+    prob = W.double_box()
+    prep = prepare_feynman(prob)
+    orc = P.feynman_problem(prob)
+    assert len(prep.units) == len(orc.units)
+    assert [(u.sector, u.order) for u in prep.units] == [(u.sector, u.order) for u in orc.units]
+    rng = np.random.default_rng(2)
+    for i in rng.choice(len(prep.units), 25, replace=False):
+        u, o = prep.units[i], orc.units[i]
+        X = rng.uniform(0.05, 1.0, size=(32, u.dim))
+        a, b = run(u.program, X), o.f_numpy(X)
+        M = P.magnitude_numpy(o, X)
+        assert np.all(np.abs(a - b) <= 1e-13 * M), i
+
+
+def test_stress_programs_sample():
+    probs = W.stress_suite(40)
+    prep = prepare_direct(probs)
+    rng = np.random.default_rng(3)
+    for k, prob in enumerate(probs):
+        orc = P.direct_problem(prob)
+        assert len(orc.units) == 1
+        X = rng.uniform(0.0, 1.0, size=(32, prob.dim))
+        a, b = run(prep.units[k].program, X), orc.units[0].f_numpy(X)
+        M = P.magnitude_numpy(orc.units[0], X)
+        assert np.all(np.abs(a - b) <= 1e-13 * M)
+
+
+def test_prefactor_matches_oracle():
+    for idx, L, k in [((1, 1), 1, 4), ((1, 1, 1, 1), 1, 3), ((1,) * 7, 2, 5), ((2, 1), 1, 3)]:
+        q1, a = PF.series(idx, L, k)
+        q2, b = prefactor_series(idx, L, k)
+        assert q1 == q2
+        assert max(abs(x - float(y)) for x, y in zip(a, b)) < 1e-13
+
+
+def test_text_format():
+    prep = parse_text("1;\n0;\nx[1]+0.2;\n|")
+    assert run(prep.units[0].program, np.array([[0.25]]))[0] == 0.45
+    prep = parse_text("2; 1; l[x[1]+x[2]]; p[f[1],2]*x[2] - 1/(1+x[1]); |")
+    X = np.array([[0.3, 0.6]])
+    assert abs(run(prep.units[0].program, X)[0] - (np.log(0.9) ** 2 * 0.6 - 1 / 1.3)) < 1e-15
+    with pytest.raises(ValueError):
+        parse_text("1; 0; x[2]; |")
+
+
+def test_validator_rejects_bad_programs():
+    prep = parse_text("1; 0; x[1]*x[1]+0.5; |")
+    prog = prep.units[0].program
+    B.validate(prog)
+    bad = B.Program(prog.code.copy(), prog.consts, prog.n_slots, prog.out_slot, prog.dim, {})
+    bad.code[0] = B.encode("ADD", 0, 3, 3)
+    with pytest.raises(ValueError):
+        B.validate(bad)
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "fiesta.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fiesta_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1511_03614_gb300 import build, _native
+    if not os.path.exists(build.LIB):
+        try:
+            build.build()
+        except Exception as e:          # no nvcc here: nothing to check
+            pytest.skip(f"cannot build the library: {e}")
+    lib = C.CDLL(build.LIB)
+    names = _declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_native.EXPORTS)
+
+
+def test_load_rejects_invalid_program_without_gpu():
+    """The validator runs before any device call, so this works on a CPU-only host."""
+    from paper_1511_03614_gb300 import build, _native as N
+    if not os.path.exists(build.LIB):
+        pytest.skip("library not built")
+    lib = N.load()
+    code = (C.c_uint32 * 1)(B.encode("ADD", 0, 1, 1))
+    cons = (C.c_double * 1)(0.0)
+    progs = (N.Program * 1)(N.Program(1, 1, 0, 2, 0, 0, 0, 0, code, cons))
+    ctx = C.c_void_p()
+    rc = lib.fiesta_load_sectors(C.byref(ctx), progs, 1, None, None)
+    assert rc == -1 and b"read before written" in lib.fiesta_last_error()

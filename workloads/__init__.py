@@ -160,8 +160,10 @@ def stress_suite(n_units: int = 10_000, seed: int = STRESS_SEED, orders=(0, 1, 2
     two polynomials with 5..40 monomials of total degree <= 3 and coefficients
     uniform in [0.1, 1] (one term is always the constant monomial so that P >= 0.1
     on the unit cube), exponents n + m*eps with n, m uniform in {-2..2}, and
-    log(P1)^j with j in {0, 1, 2}.  Coefficients are rounded to binary64.
-    Returns a list of DirectProblem.
+    log(P1)^j with j in {0, 1, 2}.  Coefficients are rounded to binary64.  Each
+    integrand contributes one unit: the coefficient of eps^K with K drawn
+    uniformly from ``orders`` (the lowest order when the integrand does not
+    depend on eps).  Returns a list of DirectProblem.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
@@ -190,6 +192,9 @@ def stress_suite(n_units: int = 10_000, seed: int = STRESS_SEED, orders=(0, 1, 2
             m = int(rng.integers(-2, 3))
             factors.append(DirectFactor(terms=terms, n=n, m=m))
         j = int(rng.integers(0, 3))
+        K = int(orders[int(rng.integers(0, len(orders)))])
+        if all(f.m == 0 for f in factors):
+            K = min(orders)          # higher coefficients of an eps-free integrand vanish
         out.append(DirectProblem(name=f"stress{u}", dim=dim, monomial=mono,
-                                 factors=tuple(factors), log_power=j, orders=tuple(orders)))
+                                 factors=tuple(factors), log_power=j, orders=(K,)))
     return out
