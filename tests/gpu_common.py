@@ -39,7 +39,7 @@ def stress(n):
     return probs, prep, Integrator(prep)
 
 
-def test_points(dim, rng, n_random=96):
+def sample_points(dim, rng, n_random=96):
     """Random interior points plus boundary points (coordinates at 2^-40, 2^-20, 1 - 2^-20, 1/2)."""
     X = [rng.uniform(0.0, 1.0, size=(n_random, dim))]
     edge = np.array([2.0 ** -40, 2.0 ** -20, 1 - 2.0 ** -20, 0.5])

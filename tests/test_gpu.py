@@ -8,15 +8,16 @@ import pytest
 import workloads as W
 from oracle import pipeline as P, vegas as V, quadrature as Q
 
-from gpu_common import need_gpu, feynman, integrator, stress, test_points
+from gpu_common import need_gpu, feynman, integrator, stress, sample_points
 
 pytestmark = pytest.mark.gpu
 
-# Tolerances.  Per point: relative 1e-12 (binary64) / 1e-5 (binary32 body) against
-# a 50-digit evaluation of the oracle's expression where all coordinates are at
-# least 1/16 away from 0; everywhere, |f_gpu - f| <= tol * M(x) with M the
-# oracle's condition-scaled magnitude (sum of absolute values of the additive
-# terms), which bounds the rounding error of any order of evaluation.
+# Tolerances.  Everywhere: |f_gpu - f| <= tol * M(x), tol = 1e-12 (binary64) or
+# 1e-5 (binary32 body), f a 50-digit evaluation of the oracle's expression and M
+# its condition-scaled magnitude (the sum of the absolute values of the additive
+# terms at every level), which bounds the rounding error of any evaluation
+# order.  Strictly relative, |f_gpu - f| <= tol * |f|, on the well-conditioned
+# points: all coordinates >= 1/16 and M <= 10 |f|.
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
@@ -30,13 +31,13 @@ def _check_points(prep, orc, idx, precision, rng):
     worst_strict = 0.0
     for i in idx:
         u, o = prep.units[i], orc.units[i]
-        X = test_points(u.dim, rng, 48)
+        X = sample_points(u.dim, rng, 48)
         f = integ.eval_batch(i, X, precision)
         ref = _ref(o, X)
         M = P.magnitude_numpy(o, X)
         tol = TOL[precision]
         assert np.all(np.abs(f - ref) <= tol * np.maximum(M, 1e-300)), (i, np.max(np.abs(f - ref) / M))
-        inner = np.all(X >= 1.0 / 16, axis=1) & (np.abs(ref) > 1e-3 * M)
+        inner = np.all(X >= 1.0 / 16, axis=1) & (10 * np.abs(ref) >= M)
         if inner.any():
             rel = np.abs(f[inner] - ref[inner]) / np.abs(ref[inner])
             worst_strict = max(worst_strict, float(rel.max()))
