@@ -173,6 +173,32 @@ int fiesta_refine(fiesta_ctx *ctx, int32_t dim, int64_t n, double alpha, double 
  */
 int fiesta_probe_peaks(double *out, int32_t n);
 
+/*
+ * One Vegas sampling pass that allocates no device memory (the paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc or an allocator while they run, for example code that must not
+ * synchronise the device, runs with a memory pool fixed at start-up, or has no
+ * allocator hooked up).  It evaluates units [unit_begin, unit_end) of ctx at
+ * `points` points each on their current grids (no adaptation) with the point
+ * stream of (seed, unit, iteration), like iteration `iteration` of
+ * fiesta_integrate with adapt = 0, and writes each unit's sample mean of
+ * v = f*J to mean[k] and its variance of the mean to var[k], k = unit -
+ * unit_begin.  mean and var are caller-owned, both host or both device arrays.
+ *
+ * Its scratch (partial sums, counters) is one file-scope device array of about
+ * 2.1 MB that every GPU loading the library keeps until the process exits.
+ * Limits: at most 16384 units and 65536 work items (items of 2048 points) per
+ * call; larger requests return FIESTA_E_INVALID with the sizes in the message.
+ * The first call on each device looks up the array's device address (a CUDA
+ * runtime query, no allocation); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * the parts that must start at zero are cleared by each call.  Calls whose
+ * work overlaps on the GPU (other streams, other threads) race on the array.
+ * Errors: FIESTA_E_INVALID, FIESTA_E_CUDA, FIESTA_E_NOMEM (shared memory).
+ */
+int fiesta_sample_noalloc(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end, int64_t points, uint64_t seed,
+                          int32_t iteration, int32_t precision, int32_t rng, double *mean, double *var);
+
 void fiesta_free(fiesta_ctx *ctx);
 const char *fiesta_last_error(void);
 int fiesta_version(void);

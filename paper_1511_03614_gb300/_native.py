@@ -60,6 +60,8 @@ EXPORTS = {
     "fiesta_refine": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double)]),
     "fiesta_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.c_int32]),
+    "fiesta_sample_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_uint64, C.c_int32,
+                                        C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "fiesta_free": (None, [C.c_void_p]),
     "fiesta_last_error": (C.c_char_p, []),
     "fiesta_version": (C.c_int, []),
