@@ -166,10 +166,11 @@ int fiesta_refine(fiesta_ctx *ctx, int32_t dim, int64_t n, double alpha, double 
 /*
  * Measurement support (no counterpart in the paper): measured throughput of
  * the arithmetic pipes on the current device, used to turn an integrand's
- * instruction mix into a lower bound on its evaluation time.  out (host, >= 6
- * doubles): [0] binary64 FMA TFLOP/s, [1] binary64 log G/s, [2] binary64
- * divide G/s, [3] binary32 FMA TFLOP/s, [4] binary32 logf G/s, [5] binary32
- * divide G/s.  Allocates and frees a small scratch buffer.
+ * instruction mix into a lower bound on its evaluation time.  out (host, >= 7
+ * doubles): [0] binary64 FMA TFLOP/s, [1] binary64 log (CUDA's) G/s, [2]
+ * binary64 divide G/s, [3] binary32 FMA TFLOP/s, [4] binary32 logf G/s, [5]
+ * binary32 divide G/s, [6] the interpreter's table-driven binary64 log G/s.
+ * Allocates and frees small scratch buffers.
  */
 int fiesta_probe_peaks(double *out, int32_t n);
 

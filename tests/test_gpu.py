@@ -224,3 +224,21 @@ def test_nonfinite_samples_are_reported():
     with pytest.raises(FiestaError) as e:
         integ.integrate(n_iter=1, points=1000)
     assert e.value.code == -5 and "unit 0" in str(e.value)
+
+
+def test_table_log_within_one_ulp():
+    """The interpreter's binary64 log (Tang's table method) against the exact value:
+    within 1 ulp, the accuracy bound CUDA documents for its own log."""
+    need_gpu()
+    from paper_1511_03614_gb300 import parse_text, Integrator
+    rng = np.random.default_rng(13)
+    x = np.concatenate([np.exp(rng.uniform(-690, 0, 4000)), 1 - rng.uniform(0, 1e-3, 500),
+                        rng.uniform(0.5, 1, 2000), [2.0 ** -1022, 0.7071067811865476, 0.70710671, 1.0]])
+    for text, scale in (("1; 0; l[x[1]]; |", 1.0), ("1; 0; l[x[1]*1e300]; |", 1e300)):
+        integ = Integrator(parse_text(text))
+        got = integ.eval_batch(0, x[:, None])
+        arg = x * scale
+        with mp.workdps(40):
+            ref = [mp.log(mp.mpf(float(a))) for a in arg]
+        ulps = [abs(mp.mpf(float(g)) - r) / math.ulp(float(r)) if float(r) != 0 else abs(g) for g, r in zip(got, ref)]
+        assert max(ulps) <= 1.0, max(ulps)
