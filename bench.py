@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "auto"])
     ap.add_argument("--points", type=int, default=0, help="points per unit per iteration (0: workload default)")
     ap.add_argument("--iters", type=int, default=0, help="Vegas iterations per step (0: workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -233,14 +233,9 @@ def run_ours(args):
     flops_per_launch = sum(f for f, _ in per_unit) * pts
     slots_per_launch = sum(s for _, s in per_unit) * pts
     avg_eval_s = eval_ms / max(eval_launches, 1) * 1e-3
-    if args.precision == "fp64":
-        achieved = 2.0 * slots_per_launch / avg_eval_s * 1e-12      # FMA-equivalent TFLOP/s
-        peak_meas = peaks[0]
-        nominal = 1.25
-    else:
-        achieved = 2.0 * slots_per_launch / avg_eval_s * 1e-12
-        peak_meas = peaks[3]
-        nominal = None
+    achieved = 2.0 * slots_per_launch / avg_eval_s * 1e-12          # FMA-equivalent TFLOP/s
+    peak_meas = peaks[0]
+    nominal = 1.25
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "TFLOP/s",
                 "frac": achieved / peak_meas, "traffic": None,
                 "kernel": "k_eval", "work": "FMA-equivalent pipe slots x 2 per launch (log/div weighted by "
@@ -284,7 +279,8 @@ def run_ours(args):
             "metric": "sampling points/s", "value": value, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32 body / f64 map+sums",
+            "dtype": {"fp64": "f64", "fp32": "f32 body, f64 map/sums/grid",
+                      "auto": "per unit f32 or f64 body, f64 map/sums/grid"}[args.precision],
             "data": "synthetic",
             "config": {"workload": {"box": "one-loop massless box s=-1 t=-2, eps^-2..eps^0, 12 sectors x 3 dims "
                                            "(32 units), Vegas 10 it x 1e6 Philox points per unit",
@@ -293,6 +289,9 @@ def run_ours(args):
                                     "stress": "10000 seeded synthetic integrands, dims 3..8, 2^20 Sobol points"
                                     }[args.workload],
                        "units": len(prep.units), "points_per_unit_per_iter": pts, "iterations": iters,
+                       "units_fp32": res.stats.get("units_fp32") if res else None,
+                       "launch_shape": {"threads": res.stats.get("threads"),
+                                        "points_per_thread": res.stats.get("points_per_thread")} if res else None,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)"},
             "roofline": roofline,

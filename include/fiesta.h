@@ -40,6 +40,7 @@ extern "C" {
 #define FIESTA_RNG_SOBOL     1
 #define FIESTA_FP64          0  /* all arithmetic in binary64 */
 #define FIESTA_FP32          1  /* integrand body in binary32; map, Jacobian, sums and grid in binary64 */
+#define FIESTA_AUTO          2  /* per unit: binary32 where a probe against binary64 stays within budget */
 
 #define FIESTA_NBINS       128  /* Vegas bins per coordinate */
 #define FIESTA_MAX_DIM       8  /* largest integration dimension */
@@ -85,10 +86,13 @@ typedef struct {
     int64_t unit_begin;       /* integrate units [unit_begin, unit_end) only ... */
     int64_t unit_end;         /* ... unit_end <= 0 means all units */
     int64_t timeout_ms;       /* device time budget per kernel launch; 0 = none */
-    int32_t threads;          /* threads per block; 0 = automatic */
+    int32_t threads;          /* threads per block (multiple of 32, <= 256; a power of two with Sobol); 0 = autotuned */
     int32_t reset_grid;       /* nonzero: start from the uniform grid (else keep the last one) */
     int32_t iter_offset;      /* added to the iteration number in the point streams */
-    int32_t reserved[5];
+    int32_t points_per_thread;/* points per thread per work item; 0 = autotuned */
+    int64_t probe_points;     /* FIESTA_AUTO: probe points per unit (0: 16384) */
+    double fp32_budget;       /* FIESTA_AUTO: largest relative error of a unit's mean accepted in binary32 (0: 1e-6) */
+    int32_t reserved[4];
 } fiesta_options;
 
 typedef struct {
@@ -98,6 +102,9 @@ typedef struct {
     int64_t n_points;         /* points evaluated for this unit */
     int32_t order, sector;
     int64_t n_nonfinite;      /* samples whose value was not finite (counted as 0) */
+    int32_t precision;        /* FIESTA_FP64 or FIESTA_FP32: how this unit was evaluated */
+    int32_t pad;
+    double fp32_error;        /* FIESTA_AUTO: probe estimate of the binary32 error of the mean (else NaN) */
 } fiesta_unit_result;
 
 typedef struct {
@@ -107,6 +114,9 @@ typedef struct {
     double points_per_s;      /* points / (gpu_ms / 1000) */
     int32_t kernels_launched; /* kernel launches made by this call */
     int32_t eval_launches;    /* of which evaluation-kernel launches */
+    int64_t units_fp32;       /* units evaluated in binary32 */
+    int32_t threads[2];       /* block size used for binary64 [0] and binary32 [1] */
+    int32_t points_per_thread[2];
 } fiesta_stats;
 
 typedef struct fiesta_ctx fiesta_ctx;
@@ -151,6 +161,18 @@ int fiesta_eval_batch(fiesta_ctx *ctx, int64_t unit, int32_t precision, const do
  * mean[i] and var[i] (variance of the mean) for i < n_iter, host arrays.
  */
 int fiesta_iterations(fiesta_ctx *ctx, int64_t unit, int32_t n_iter, double *mean, double *var);
+
+/*
+ * Per-unit binary32 probe (the precision policy of FIESTA_AUTO): evaluate
+ * units [unit_begin, unit_end) at n_points Philox points through their
+ * current grids in binary64 and in binary32 and return, per unit, the
+ * relative error of the binary32 sample mean (err_mean) and the largest
+ * pointwise difference divided by the mean |f J| (err_max).  Host arrays of
+ * unit_end - unit_begin doubles.  The paper's counterpart is the mixed
+ * MPFR/double mode of its integration workers (Sec. 4.6, MPFR/Native/Mixed).
+ */
+int fiesta_precision_probe(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end, int64_t n_points, uint64_t seed,
+                           double *err_mean, double *err_max);
 
 /* Copy one unit's Vegas grid (dim * (FIESTA_NBINS+1) edges, row per coordinate)
  * to the host array `grid`, or set it from `grid` (checkpoint and resume). */

@@ -10,7 +10,7 @@ FIESTA_OK = 0
 ERRORS = {-1: "FIESTA_E_INVALID", -2: "FIESTA_E_NOMEM", -3: "FIESTA_E_CUDA",
           -4: "FIESTA_E_TIMEOUT", -5: "FIESTA_E_NONFINITE"}
 RNG = {"philox": 0, "sobol": 1}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "auto": 2}
 NBINS = 128
 MAX_DIM = 8
 
@@ -34,17 +34,20 @@ class Options(C.Structure):
                 ("points_per_iter", C.c_int64), ("seed", C.c_uint64), ("alpha", C.c_double),
                 ("skip_first", C.c_int32), ("order_lo", C.c_int32), ("unit_begin", C.c_int64),
                 ("unit_end", C.c_int64), ("timeout_ms", C.c_int64), ("threads", C.c_int32),
-                ("reset_grid", C.c_int32), ("iter_offset", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("reset_grid", C.c_int32), ("iter_offset", C.c_int32), ("points_per_thread", C.c_int32),
+                ("probe_points", C.c_int64), ("fp32_budget", C.c_double), ("reserved", C.c_int32 * 4)]
 
 
 class UnitResult(C.Structure):
     _fields_ = [("value", C.c_double), ("sigma", C.c_double), ("chi2_dof", C.c_double), ("n_points", C.c_int64),
-                ("order", C.c_int32), ("sector", C.c_int32), ("n_nonfinite", C.c_int64)]
+                ("order", C.c_int32), ("sector", C.c_int32), ("n_nonfinite", C.c_int64), ("precision", C.c_int32),
+                ("pad", C.c_int32), ("fp32_error", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("gpu_ms", C.c_double), ("eval_ms", C.c_double), ("points", C.c_int64),
-                ("points_per_s", C.c_double), ("kernels_launched", C.c_int32), ("eval_launches", C.c_int32)]
+                ("points_per_s", C.c_double), ("kernels_launched", C.c_int32), ("eval_launches", C.c_int32),
+                ("units_fp32", C.c_int64), ("threads", C.c_int32 * 2), ("points_per_thread", C.c_int32 * 2)]
 
 
 EXPORTS = {
@@ -55,6 +58,8 @@ EXPORTS = {
     "fiesta_eval_batch": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]),
     "fiesta_iterations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
+    "fiesta_precision_probe": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_uint64,
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "fiesta_get_grid": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "fiesta_set_grid": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "fiesta_refine": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.POINTER(C.c_double),

@@ -74,14 +74,16 @@ class Integrator:
     # ------------------------------------------------------------------ integrate
     def integrate(self, n_iter=10, points=100_000, seed=1, rng="philox", precision="fp64", adapt=True,
                   alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
-                  iter_offset=0, assemble_result=True, raise_nonfinite=True):
+                  iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
+                  probe_points=0, fp32_budget=0.0):
         orders = [u.order for u in self.prep.units]
         lo, hi = min(orders), max(orders)
         nord = hi - lo + 1
         b, e = (0, len(self.prep.units)) if units is None else units
         opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(bool(adapt)), int(points),
                         int(seed) & 0xFFFFFFFFFFFFFFFF, float(alpha), int(bool(skip_first)), lo, int(b), int(e),
-                        int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset))
+                        int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset),
+                        int(points_per_thread), int(probe_points), float(fp32_budget))
         val = (C.c_double * nord)()
         err = (C.c_double * nord)()
         per = (N.UnitResult * (e - b))()
@@ -93,9 +95,11 @@ class Integrator:
         values = {lo + k: val[k] for k in range(nord)}
         errors = {lo + k: err[k] for k in range(nord)}
         pu = [dict(value=r.value, sigma=r.sigma, chi2_dof=r.chi2_dof, n_points=r.n_points, order=r.order,
-                   sector=r.sector, n_nonfinite=r.n_nonfinite) for r in per]
+                   sector=r.sector, n_nonfinite=r.n_nonfinite, precision=("fp64", "fp32")[r.precision],
+                   fp32_error=r.fp32_error) for r in per]
         stats = dict(gpu_ms=st.gpu_ms, eval_ms=st.eval_ms, points=st.points, points_per_s=st.points_per_s,
-                     kernels_launched=st.kernels_launched, eval_launches=st.eval_launches)
+                     kernels_launched=st.kernels_launched, eval_launches=st.eval_launches,
+                     units_fp32=st.units_fp32, threads=tuple(st.threads), points_per_thread=tuple(st.points_per_thread))
         res = Result(values, errors, pu, stats)
         if assemble_result and units is None:
             res.assembled, res.assembled_errors = assemble(self.prep, values, errors)
@@ -118,6 +122,16 @@ class Integrator:
             N.check(self.lib.fiesta_eval_batch(self.ctx, int(unit), N.PRECISION[precision],
                                                x.ctypes.data_as(C.c_void_p), x.shape[0], f.ctypes.data_as(C.c_void_p)))
         return f
+
+    def precision_probe(self, n_points=16384, seed=1, units=None):
+        """Per unit (err_mean, err_max) of binary32 against binary64 at the same points."""
+        b, e = (0, len(self.prep.units)) if units is None else units
+        m = np.empty(e - b)
+        x = np.empty(e - b)
+        N.check(self.lib.fiesta_precision_probe(self.ctx, b, e, int(n_points), int(seed),
+                                                m.ctypes.data_as(C.POINTER(C.c_double)),
+                                                x.ctypes.data_as(C.POINTER(C.c_double))))
+        return m, x
 
     def iterations(self, unit, n_iter):
         m = (C.c_double * n_iter)()

@@ -242,3 +242,59 @@ def test_table_log_within_one_ulp():
             ref = [mp.log(mp.mpf(float(a))) for a in arg]
         ulps = [abs(mp.mpf(float(g)) - r) / math.ulp(float(r)) if float(r) != 0 else abs(g) for g, r in zip(got, ref)]
         assert max(ulps) <= 1.0, max(ulps)
+
+
+def test_precision_probe_and_auto_mode():
+    """The per-unit binary32 probe and FIESTA_AUTO: box results stay within errors of the closed form."""
+    need_gpu()
+    prep, _ = feynman("box")
+    integ = integrator("box")
+    em, ex = integ.precision_probe(n_points=16384, seed=4)
+    em2, ex2 = integ.precision_probe(n_points=16384, seed=4)
+    assert np.array_equal(em, em2) and np.array_equal(ex, ex2)          # deterministic
+    assert np.all(em < 1e-5) and np.all(np.isfinite(ex))
+    res = integ.integrate(n_iter=6, points=400_000, seed=4, precision="auto", fp32_budget=1e-6)
+    exact = {-2: 2.0, -1: -math.log(2.0), 0: -2 * math.pi ** 2 / 3}
+    for n, v in exact.items():
+        s = res.assembled_errors[n]
+        assert abs(res.assembled[n] - v) < 4 * s + 1e-6, (n, res.assembled[n], v, s)
+    used = [u["precision"] for u in res.per_unit]
+    assert used.count("fp32") == res.stats["units_fp32"]
+    for u in res.per_unit:
+        assert (u["precision"] == "fp32") == (u["fp32_error"] <= 1e-6)
+        assert u["fp32_error"] < 1e-5
+
+
+def test_block_shape_does_not_change_the_points():
+    """Autotuned and fixed launch shapes evaluate the same point streams."""
+    need_gpu()
+    integ = integrator("box")
+    a = integ.integrate(n_iter=1, points=300_000, seed=8, adapt=False, threads=128, points_per_thread=16)
+    b = integ.integrate(n_iter=1, points=300_000, seed=8, adapt=False, threads=0, points_per_thread=0)
+    c = integ.integrate(n_iter=1, points=300_000, seed=8, adapt=False, threads=64, points_per_thread=32)
+    for x, y, z in zip(a.per_unit, b.per_unit, c.per_unit):
+        scale = abs(x["value"]) + x["sigma"] * 1e3
+        assert abs(x["value"] - y["value"]) <= 1e-12 * scale
+        assert abs(x["value"] - z["value"]) <= 1e-12 * scale
+
+
+def test_stress_low_dim_against_gauss_legendre():
+    """Three-dimensional stress integrands (smooth, P >= 0.1): Sobol estimate vs a
+    tensor Gauss-Legendre rule of the oracle's integrand."""
+    need_gpu()
+    probs, prep, integ = stress(64)
+    res = integ.integrate(n_iter=1, points=1 << 18, seed=12, rng="sobol", adapt=False)
+    xg, wg = np.polynomial.legendre.leggauss(24)
+    xg, wg = (xg + 1) / 2, wg / 2
+    checked = 0
+    for k, prob in enumerate(probs):
+        if prob.dim != 3:
+            continue
+        o = P.direct_problem(prob).units[0]
+        X = np.stack(np.meshgrid(xg, xg, xg, indexing="ij"), -1).reshape(-1, 3)
+        Wt = np.einsum("i,j,k->ijk", wg, wg, wg).ravel()
+        truth = float(np.sum(Wt * o.f_numpy(X)))
+        r = res.per_unit[k]
+        assert abs(r["value"] - truth) <= 3 * r["sigma"] + 1e-9 * abs(truth), (k, r["value"], truth, r["sigma"])
+        checked += 1
+    assert checked >= 3

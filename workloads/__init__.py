@@ -153,11 +153,26 @@ class DirectProblem:
 STRESS_SEED = 1511036140
 
 
+def _monomials_up_to_degree3(dim):
+    """Exponent tuples of total degree 1..3 in ``dim`` variables, in a fixed order."""
+    out = []
+    for deg in (1, 2, 3):
+        def rec(i, left, cur):
+            if i == dim - 1:
+                out.append(tuple(cur + [left]))
+                return
+            for k in range(left, -1, -1):
+                rec(i + 1, left - k, cur + [k])
+        rec(0, deg, [])
+    return out
+
+
 def stress_suite(n_units: int = 10_000, seed: int = STRESS_SEED, orders=(0, 1, 2)):
     """The seeded synthetic stress suite.
 
     Each integrand has dim uniform in 3..8, monomial exponents k_i in {0..3},
-    two polynomials with 5..40 monomials of total degree <= 3 and coefficients
+    two polynomials with 5..40 distinct monomials of total degree <= 3 (at most
+    all of them when there are fewer) and coefficients
     uniform in [0.1, 1] (one term is always the constant monomial so that P >= 0.1
     on the unit cube), exponents n + m*eps with n, m uniform in {-2..2}, and
     log(P1)^j with j in {0, 1, 2}.  Coefficients are rounded to binary64.  Each
@@ -171,21 +186,11 @@ def stress_suite(n_units: int = 10_000, seed: int = STRESS_SEED, orders=(0, 1, 2
         dim = int(rng.integers(3, 9))
         mono = tuple(int(v) for v in rng.integers(0, 4, size=dim))
         factors = []
+        monos = _monomials_up_to_degree3(dim)
         for _ in range(2):
-            nterms = int(rng.integers(5, 41))
-            seen = {tuple([0] * dim)}
-            exps = [tuple([0] * dim)]
-            tries = 0
-            while len(exps) < nterms and tries < 10_000:
-                tries += 1
-                deg = int(rng.integers(1, 4))
-                e = [0] * dim
-                for _k in range(deg):
-                    e[int(rng.integers(0, dim))] += 1
-                e = tuple(e)
-                if e not in seen:
-                    seen.add(e)
-                    exps.append(e)
+            nterms = min(int(rng.integers(5, 41)), len(monos) + 1)
+            pick = rng.choice(len(monos), size=nterms - 1, replace=False)
+            exps = [tuple([0] * dim)] + [monos[i] for i in sorted(pick)]
             coefs = rng.uniform(0.1, 1.0, size=len(exps))
             terms = tuple((float(c), e) for c, e in zip(coefs, exps))
             n = int(rng.integers(-2, 3))
