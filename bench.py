@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--iters", type=int, default=0, help="Vegas iterations per step (0: workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "tta"],
+                    help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
+    ap.add_argument("--target", type=float, default=1e-4)
     return ap.parse_args()
 
 
@@ -194,7 +197,8 @@ def run_ours(args):
     N.check(lib.fiesta_probe_peaks(peaks, 7))
     peaks = list(peaks)
     integ = Integrator(prep)
-    kw = dict(n_iter=iters, points=pts, seed=1, rng=rng, precision=args.precision)
+    # replicas: every rank integrates every unit with its own point streams (weak scaling)
+    kw = dict(n_iter=iters, points=pts, seed=1 + rank, rng=rng, precision=args.precision)
     for _ in range(args.warmup):
         integ.integrate(**kw)
     torch.cuda.synchronize()
@@ -367,10 +371,42 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_tta(args):
+    """GPU-seconds to the target relative error per eps order: plain binary64 Vegas
+    against the per-unit mixed precision policy and binary32, same GPU, same points."""
+    import torch
+    from paper_1511_03614_gb300 import Integrator
+    from paper_1511_03614_gb300.api import run_to_accuracy
+    torch.cuda.set_device(0)
+    pts = args.points or {"box": 1_000_000, "double_box": 2_000_000, "bubble": 200_000}.get(args.workload, 1_000_000)
+    prep = prepared(args.workload)
+    out = {"mode": "tta", "workload": args.workload, "target": args.target, "points_per_unit_per_iter": pts,
+           "units": len(prep.units), "runs": {}}
+    from paper_1511_03614_gb300._native import FiestaError
+    for prec in ("fp64", "auto", "fp32"):
+        integ = Integrator(prep)
+        try:
+            integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
+            r = run_to_accuracy(integ, target=args.target, points=pts, precision=prec, max_iters=400)
+        except FiestaError as e:
+            out["runs"][prec] = {"error": str(e)}
+            integ.close()
+            continue
+        out["runs"][prec] = {"gpu_s": r["gpu_s"], "points": r["points"], "iterations": r["iterations"],
+                             "converged": r["converged"],
+                             "values": {str(n): [r["values"][n], r["errors"][n]] for n in r["values"]}}
+        integ.close()
+    base = out["runs"].get("fp64", {}).get("gpu_s")
+    out["speedup_vs_fp64"] = {k: base / v["gpu_s"] for k, v in out["runs"].items() if base and "gpu_s" in v}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "tta":
+        run_tta(args)
     else:
         run_ours(args)
 

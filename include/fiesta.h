@@ -77,7 +77,7 @@ typedef struct {
     int32_t rng;              /* FIESTA_RNG_PHILOX or FIESTA_RNG_SOBOL */
     int32_t precision;        /* FIESTA_FP64 or FIESTA_FP32 */
     int32_t n_iter;           /* Vegas iterations, >= 1 */
-    int32_t adapt;            /* nonzero: refine each unit's grid between iterations */
+    int32_t adapt;            /* 1: refine each unit's grid between iterations; 2: also after the last one */
     int64_t points_per_iter;  /* sampling points per unit per iteration, >= 2 */
     uint64_t seed;            /* first Philox key word is seed mod 2^32 */
     double alpha;             /* grid damping exponent (1.5) */

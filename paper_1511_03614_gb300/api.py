@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import ctypes as C
 import dataclasses
+import math
 
 import numpy as np
 
@@ -80,7 +81,7 @@ class Integrator:
         lo, hi = min(orders), max(orders)
         nord = hi - lo + 1
         b, e = (0, len(self.prep.units)) if units is None else units
-        opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(bool(adapt)), int(points),
+        opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(adapt), int(points),
                         int(seed) & 0xFFFFFFFFFFFFFFFF, float(alpha), int(bool(skip_first)), lo, int(b), int(e),
                         int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset),
                         int(points_per_thread), int(probe_points), float(fp32_budget))
@@ -168,3 +169,129 @@ class Integrator:
             self.close()
         except Exception:
             pass
+
+
+CHECKPOINT_MAGIC = b"FIESTACK"
+CHECKPOINT_VERSION = 1
+
+
+def save_checkpoint(path, integ, state):
+    """Write the Vegas state (every unit's grid, the running weighted sums, the
+    iteration count and the stream seed) to ``path``: magic, version, a JSON
+    header and the float64 payload, protected by a CRC-32.  The paper's pool
+    keeps per-integral partial results for restarts (``-continue``, Sec. 4.5)."""
+    import json
+    import struct
+    import zlib
+    grids = [integ.get_grid(k) for k in range(len(integ.prep.units))]
+    header = json.dumps({"n_units": len(grids), "dims": [g.shape[0] for g in grids], "it": state["it"],
+                         "seed": state["seed"], "precision": state["precision"], "rng": state["rng"],
+                         "points": state["points"], "gpu_ms": state["gpu_ms"],
+                         "points_done": state["points_done"]}).encode()
+    payload = np.concatenate([g.ravel() for g in grids] + [state["sw"], state["swi"]]).astype("<f8").tobytes()
+    body = struct.pack("<I", len(header)) + header + payload
+    with open(path + ".tmp", "wb") as f:
+        f.write(CHECKPOINT_MAGIC + struct.pack("<II", CHECKPOINT_VERSION, zlib.crc32(body)) + body)
+    import os
+    os.replace(path + ".tmp", path)
+
+
+def load_checkpoint(path, integ=None):
+    """Read a checkpoint written by save_checkpoint; verify it and, given an
+    Integrator, restore its grids.  Raises ValueError on a damaged file."""
+    import json
+    import struct
+    import zlib
+    raw = open(path, "rb").read()
+    if len(raw) < 16 or raw[:8] != CHECKPOINT_MAGIC:
+        raise ValueError("not a checkpoint file")
+    version, crc = struct.unpack("<II", raw[8:16])
+    if version != CHECKPOINT_VERSION:
+        raise ValueError(f"unsupported checkpoint version {version}")
+    body = raw[16:]
+    if zlib.crc32(body) != crc:
+        raise ValueError("checkpoint checksum mismatch (file damaged or truncated)")
+    (hl,) = struct.unpack("<I", body[:4])
+    h = json.loads(body[4:4 + hl].decode())
+    data = np.frombuffer(body[4 + hl:], dtype="<f8")
+    n = h["n_units"]
+    need = sum(d * (N.NBINS + 1) for d in h["dims"]) + 2 * n
+    if data.size != need:
+        raise ValueError("checkpoint payload has the wrong size")
+    grids = []
+    off = 0
+    for d in h["dims"]:
+        grids.append(data[off:off + d * (N.NBINS + 1)].reshape(d, N.NBINS + 1))
+        off += d * (N.NBINS + 1)
+    sw = data[off:off + n].copy()
+    swi = data[off + n:off + 2 * n].copy()
+    if integ is not None:
+        if len(integ.prep.units) != n or any(u.dim != d for u, d in zip(integ.prep.units, h["dims"])):
+            raise ValueError("checkpoint does not match these units")
+        for k, g in enumerate(grids):
+            integ.set_grid(k, g)
+    state = dict(h, sw=sw, swi=swi, grids=grids)
+    return state
+
+
+def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_iters=200, seed=1,
+                    precision="fp64", rng="philox", floor=1e-3, skip_first=1, checkpoint=None, resume=None,
+                    stop_after=None):
+    """Vegas until every eps order of the assembled result has sigma <= target * max(|R|, floor * max|R|).
+
+    Iterations are combined per unit with inverse-variance weights across calls
+    (the first ``skip_first`` iterations, spent adapting the grid, are left out),
+    units are summed per order with mean-square errors (Sec. 4.3 of the paper)
+    and the prefactor series is multiplied in.  ``checkpoint`` writes the state
+    after every call; ``resume`` continues from such a file with the same point
+    streams (iteration numbers continue); ``stop_after`` ends after that many
+    iterations (to emulate an interrupted job).  Returns a dict with the GPU
+    seconds (the library's device time over all calls), the points, the
+    iterations and the final values and errors.
+    """
+    prep = integ.prep
+    nu = len(prep.units)
+    sw = np.zeros(nu)
+    swi = np.zeros(nu)
+    gpu_ms = 0.0
+    points_done = 0
+    it = 0
+    res = None
+    if resume is not None:
+        st = load_checkpoint(resume, integ)
+        sw, swi, it = st["sw"], st["swi"], st["it"]
+        gpu_ms, points_done, seed = st["gpu_ms"], st["points_done"], st["seed"]
+    while it < max_iters:
+        r = integ.integrate(n_iter=iters_per_call, points=points, seed=seed, rng=rng, precision=precision,
+                            adapt=2, reset_grid=(it == 0), iter_offset=it, assemble_result=False)
+        gpu_ms += r.stats["gpu_ms"]
+        points_done += r.stats["points"]
+        for k in range(nu):
+            m, v = integ.iterations(k, iters_per_call)
+            for j in range(iters_per_call):
+                if it + j < skip_first:
+                    continue
+                w = 1.0 / v[j] if v[j] > 0 else 1e300
+                sw[k] += w
+                swi[k] += w * m[j]
+        it += iters_per_call
+        if checkpoint is not None:
+            save_checkpoint(checkpoint, integ, dict(it=it, seed=seed, precision=precision, rng=rng, points=points,
+                                                    gpu_ms=gpu_ms, points_done=points_done, sw=sw, swi=swi))
+        if it <= skip_first:
+            continue
+        val = swi / sw
+        sig = np.sqrt(1.0 / sw)
+        values, errors = {}, {}
+        for k, u in enumerate(prep.units):
+            values[u.order] = values.get(u.order, 0.0) + val[k]
+            errors[u.order] = errors.get(u.order, 0.0) + sig[k] ** 2
+        errors = {K: math.sqrt(e) for K, e in errors.items()}
+        R, E = assemble(prep, values, errors)
+        big = max(abs(v) for v in R.values())
+        ok = all(E[n] <= target * max(abs(R[n]), floor * big) for n in R)
+        res = dict(gpu_s=gpu_ms * 1e-3, points=points_done, iterations=it, values=R, errors=E, converged=ok,
+                   unit_values=val.copy(), unit_sigmas=sig.copy())
+        if ok or (stop_after is not None and it >= stop_after):
+            break
+    return res

@@ -298,3 +298,18 @@ def test_stress_low_dim_against_gauss_legendre():
         assert abs(r["value"] - truth) <= 3 * r["sigma"] + 1e-9 * abs(truth), (k, r["value"], truth, r["sigma"])
         checked += 1
     assert checked >= 3
+
+
+def test_checkpoint_resume_continues_the_same_streams(tmp_path):
+    """An interrupted run resumed from its checkpoint gives the uninterrupted run's results."""
+    need_gpu()
+    from paper_1511_03614_gb300 import Integrator
+    from paper_1511_03614_gb300.api import run_to_accuracy
+    prep, _ = feynman("bubble")
+    full = run_to_accuracy(Integrator(prep), target=1e-12, points=50_000, max_iters=6, seed=5)
+    ck = str(tmp_path / "bubble.ck")
+    run_to_accuracy(Integrator(prep), target=1e-12, points=50_000, max_iters=6, seed=5, checkpoint=ck, stop_after=2)
+    resumed = run_to_accuracy(Integrator(prep), target=1e-12, points=50_000, max_iters=6, seed=5, resume=ck)
+    assert resumed["iterations"] == full["iterations"] == 6
+    d = np.abs(resumed["unit_values"] - full["unit_values"])
+    assert np.all(d <= 1e-9 * (np.abs(full["unit_values"]) + full["unit_sigmas"]))
