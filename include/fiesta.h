@@ -222,6 +222,46 @@ int fiesta_probe_peaks(double *out, int32_t n);
 int fiesta_sample_noalloc(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end, int64_t points, uint64_t seed,
                           int32_t iteration, int32_t precision, int32_t rng, double *mean, double *var);
 
+/*
+ * Learned proposal (not in the paper): per unit, a normalising flow over the
+ * unit cube that stands in for the Vegas map.  Four affine coupling layers in
+ * logit space, each with an MLP 16 -> 64 -> 64 -> 16 (ReLU); the sampler runs
+ * the MLPs on the tensor cores in BF16 with FP32 accumulation; training runs
+ * in binary32 with Adam.  Parameters: FIESTA_FLOW_PARAMS floats per unit, per
+ * layer W1[16][64], b1[64], W2[64][64], b2[64], W3[64][16] (outputs 0..7 the
+ * scales, 8..15 the shifts), b3[16].
+ *
+ * fiesta_flow_init: allocate the flows of every unit of ctx (about 450 KB per
+ *   unit with the Adam state and the packed copy) and initialise them to the
+ *   identity map (zero output layer, random hidden layers, Philox seeded).
+ * fiesta_flow_params: copy one unit's binary32 parameters to (set = 0) or from
+ *   (set != 0) the host array `params`.
+ * fiesta_flow_sample: one importance-sampling pass over units [unit_begin,
+ *   unit_end): `points` points per unit from the flow (Philox stream of (seed,
+ *   unit, iteration)), the integrand evaluated in `precision`; writes the per-
+ *   unit mean of f/q and its variance of the mean to host arrays mean, var.
+ *   The first `keep` points of each unit are kept for training.
+ * fiesta_flow_train: `steps` Adam steps (learning rate lr) on the kept points,
+ *   loss -sum_i w_i log q(x_i) with w_i proportional to (|f_i|/q_i)^power
+ *   (power 1: KL divergence, 2: variance); `loss` (nullable, host) receives the
+ *   last step's loss per unit.
+ * fiesta_flow_check: parity hook for one unit: the sampler at the caller's base
+ *   points z (n x dim, host) gives x, log q and f; the training pass at those x
+ *   with the caller's weights w gives log q (binary32), the loss and its
+ *   gradient (FIESTA_FLOW_PARAMS floats).  All arrays host.
+ * Errors: FIESTA_E_INVALID, FIESTA_E_NOMEM, FIESTA_E_CUDA, FIESTA_E_NONFINITE.
+ */
+#define FIESTA_FLOW_PARAMS 25152
+int fiesta_flow_init(fiesta_ctx *ctx, uint64_t seed, double init_scale);
+int fiesta_flow_params(fiesta_ctx *ctx, int64_t unit, float *params, int32_t set);
+int fiesta_flow_sample(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end, int64_t points, uint64_t seed,
+                       int32_t iteration, int32_t precision, int64_t keep, double *mean, double *var,
+                       fiesta_stats *stats);
+int fiesta_flow_train(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end, int32_t steps, double lr, int32_t power,
+                      double *loss, fiesta_stats *stats);
+int fiesta_flow_check(fiesta_ctx *ctx, int64_t unit, int64_t n, int32_t precision, const double *z, double *x,
+                      double *logq, double *f, const double *w, double *logq_train, double *loss, float *grad);
+
 void fiesta_free(fiesta_ctx *ctx);
 const char *fiesta_last_error(void);
 int fiesta_version(void);

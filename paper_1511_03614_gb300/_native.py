@@ -13,6 +13,7 @@ RNG = {"philox": 0, "sobol": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "auto": 2}
 NBINS = 128
 MAX_DIM = 8
+FLOW_PARAMS = 4 * (16 * 64 + 64 + 64 * 64 + 64 + 64 * 16 + 16)
 
 
 class Program(C.Structure):
@@ -67,6 +68,16 @@ EXPORTS = {
     "fiesta_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.c_int32]),
     "fiesta_sample_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_uint64, C.c_int32,
                                         C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "fiesta_flow_init": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double]),
+    "fiesta_flow_params": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_float), C.c_int32]),
+    "fiesta_flow_sample": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_uint64, C.c_int32, C.c_int32,
+                                     C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(Stats)]),
+    "fiesta_flow_train": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_double, C.c_int32,
+                                    C.POINTER(C.c_double), C.POINTER(Stats)]),
+    "fiesta_flow_check": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_float)]),
     "fiesta_free": (None, [C.c_void_p]),
     "fiesta_last_error": (C.c_char_p, []),
     "fiesta_version": (C.c_int, []),

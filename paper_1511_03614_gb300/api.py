@@ -134,6 +134,59 @@ class Integrator:
                                                 x.ctypes.data_as(C.POINTER(C.c_double))))
         return m, x
 
+    # ------------------------------------------------------------------ learned proposal
+    def flow_init(self, seed=1, scale=0.05):
+        """Per-unit flows: random hidden weights, zero output layer (identity map)."""
+        N.check(self.lib.fiesta_flow_init(self.ctx, int(seed), float(scale)))
+
+    def flow_params(self, unit):
+        p = np.empty(N.FLOW_PARAMS, dtype=np.float32)
+        N.check(self.lib.fiesta_flow_params(self.ctx, int(unit), p.ctypes.data_as(C.POINTER(C.c_float)), 0))
+        return p
+
+    def set_flow_params(self, unit, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        N.check(self.lib.fiesta_flow_params(self.ctx, int(unit), p.ctypes.data_as(C.POINTER(C.c_float)), 1))
+
+    def flow_sample(self, points, seed=1, iteration=0, precision="fp32", keep=0, units=None):
+        """One pass of flow importance sampling: per-unit mean of f/q and its variance."""
+        b, e = (0, len(self.prep.units)) if units is None else units
+        m = np.empty(e - b)
+        v = np.empty(e - b)
+        st = N.Stats()
+        N.check(self.lib.fiesta_flow_sample(self.ctx, b, e, int(points), int(seed), int(iteration),
+                                            N.PRECISION[precision], int(keep),
+                                            m.ctypes.data_as(C.POINTER(C.c_double)),
+                                            v.ctypes.data_as(C.POINTER(C.c_double)), C.byref(st)))
+        return m, v, dict(gpu_ms=st.gpu_ms, points=st.points, kernels_launched=st.kernels_launched)
+
+    def flow_train(self, steps, lr=1e-3, power=1, units=None):
+        b, e = (0, len(self.prep.units)) if units is None else units
+        loss = np.empty(e - b)
+        st = N.Stats()
+        N.check(self.lib.fiesta_flow_train(self.ctx, b, e, int(steps), float(lr), int(power),
+                                           loss.ctypes.data_as(C.POINTER(C.c_double)), C.byref(st)))
+        return loss, dict(gpu_ms=st.gpu_ms, kernels_launched=st.kernels_launched)
+
+    def flow_check(self, unit, z, w, precision="fp64"):
+        """Sampler outputs at given base points z and the training pass (log q, loss,
+        gradient) at the sampled x with weights w; for parity checks."""
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        n, d = z.shape
+        x = np.empty((n, d))
+        lq = np.empty(n)
+        f = np.empty(n)
+        lqt = np.empty(n)
+        loss = np.empty(1)
+        g = np.empty(N.FLOW_PARAMS, dtype=np.float32)
+        dp = C.POINTER(C.c_double)
+        N.check(self.lib.fiesta_flow_check(self.ctx, int(unit), n, N.PRECISION[precision], z.ctypes.data_as(dp),
+                                           x.ctypes.data_as(dp), lq.ctypes.data_as(dp), f.ctypes.data_as(dp),
+                                           w.ctypes.data_as(dp), lqt.ctypes.data_as(dp), loss.ctypes.data_as(dp),
+                                           g.ctypes.data_as(C.POINTER(C.c_float))))
+        return dict(x=x, logq=lq, f=f, logq_train=lqt, loss=loss[0], grad=g)
+
     def iterations(self, unit, n_iter):
         m = (C.c_double * n_iter)()
         v = (C.c_double * n_iter)()
@@ -293,5 +346,52 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
         res = dict(gpu_s=gpu_ms * 1e-3, points=points_done, iterations=it, values=R, errors=E, converged=ok,
                    unit_values=val.copy(), unit_sigmas=sig.copy())
         if ok or (stop_after is not None and it >= stop_after):
+            break
+    return res
+
+
+def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, steps_per_round=20, lr=2e-3,
+             power=1, max_rounds=200, seed=1, precision="fp32", floor=1e-3, skip_rounds=None):
+    """Learned proposal: per unit, alternate flow sampling (an unbiased estimate each
+    round) and training on the round's kept points; stop when every eps order meets
+    the target (same rule as run_to_accuracy).  Rounds while training are combined
+    too, with inverse-variance weights, except the first ``skip_rounds`` (default:
+    half of the training rounds).  GPU seconds include the training."""
+    prep = integ.prep
+    nu = len(prep.units)
+    integ.flow_init(seed=seed)
+    skip = train_rounds // 2 if skip_rounds is None else skip_rounds
+    sw = np.zeros(nu)
+    swi = np.zeros(nu)
+    gpu_ms = 0.0
+    pts = 0
+    res = None
+    for r in range(max_rounds):
+        m, v, st = integ.flow_sample(points, seed=seed, iteration=r, precision=precision,
+                                     keep=keep if r < train_rounds else 0)
+        gpu_ms += st["gpu_ms"]
+        pts += st["points"]
+        if r >= skip:
+            w = np.where(v > 0, 1.0 / np.maximum(v, 1e-300), 1e300)
+            sw += w
+            swi += w * m
+        if r < train_rounds:
+            _, tst = integ.flow_train(steps_per_round, lr=lr, power=power)
+            gpu_ms += tst["gpu_ms"]
+        if r < skip:
+            continue
+        val = swi / sw
+        sig = np.sqrt(1.0 / sw)
+        values, errors = {}, {}
+        for k, u in enumerate(prep.units):
+            values[u.order] = values.get(u.order, 0.0) + val[k]
+            errors[u.order] = errors.get(u.order, 0.0) + sig[k] ** 2
+        errors = {K: math.sqrt(e) for K, e in errors.items()}
+        R, E = assemble(prep, values, errors)
+        big = max(abs(x) for x in R.values())
+        ok = all(E[n] <= target * max(abs(R[n]), floor * big) for n in R)
+        res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=r + 1, values=R, errors=E, converged=ok,
+                   unit_values=val.copy(), unit_sigmas=sig.copy())
+        if ok and r >= train_rounds:
             break
     return res
