@@ -396,6 +396,18 @@ def run_tta(args):
                              "converged": r["converged"],
                              "values": {str(n): [r["values"][n], r["errors"][n]] for n in r["values"]}}
         integ.close()
+    # learned proposal: flow sampling with training rounds, binary32 integrand
+    from paper_1511_03614_gb300.api import run_flow
+    integ = Integrator(prep)
+    try:
+        r = run_flow(integ, target=args.target, points=pts, keep=4096, train_rounds=8, steps_per_round=20,
+                     max_rounds=300, precision="fp32")
+        out["runs"]["flow_fp32"] = {"gpu_s": r["gpu_s"], "points": r["points"], "rounds": r["rounds"],
+                                    "converged": r["converged"],
+                                    "values": {str(n): [r["values"][n], r["errors"][n]] for n in r["values"]}}
+    except FiestaError as e:
+        out["runs"]["flow_fp32"] = {"error": str(e)}
+    integ.close()
     base = out["runs"].get("fp64", {}).get("gpu_s")
     out["speedup_vs_fp64"] = {k: base / v["gpu_s"] for k, v in out["runs"].items() if base and "gpu_s" in v}
     print(json.dumps(out))

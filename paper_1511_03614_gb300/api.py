@@ -288,7 +288,7 @@ def load_checkpoint(path, integ=None):
 
 
 def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_iters=200, seed=1,
-                    precision="fp64", rng="philox", floor=1e-3, skip_first=1, checkpoint=None, resume=None,
+                    precision="fp64", rng="philox", floor=1e-2, skip_first=1, checkpoint=None, resume=None,
                     stop_after=None):
     """Vegas until every eps order of the assembled result has sigma <= target * max(|R|, floor * max|R|).
 
@@ -351,7 +351,7 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
 
 
 def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, steps_per_round=20, lr=2e-3,
-             power=1, max_rounds=200, seed=1, precision="fp32", floor=1e-3, skip_rounds=None):
+             power=1, max_rounds=200, seed=1, precision="fp32", floor=1e-2, skip_rounds=None):
     """Learned proposal: per unit, alternate flow sampling (an unbiased estimate each
     round) and training on the round's kept points; stop when every eps order meets
     the target (same rule as run_to_accuracy).  Rounds while training are combined

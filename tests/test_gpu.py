@@ -313,3 +313,18 @@ def test_checkpoint_resume_continues_the_same_streams(tmp_path):
     assert resumed["iterations"] == full["iterations"] == 6
     d = np.abs(resumed["unit_values"] - full["unit_values"])
     assert np.all(d <= 1e-9 * (np.abs(full["unit_values"]) + full["unit_sigmas"]))
+
+
+def test_double_box_strategy_invariance():
+    """Sector sums do not depend on the decomposition strategy (M: 293 sectors, R: 313)."""
+    need_gpu()
+    import workloads as W
+    from paper_1511_03614_gb300 import prepare_feynman, Integrator
+    res = {}
+    for strat in ("M", "R"):
+        prep = prepare_feynman(W.double_box(), strategy=strat)
+        res[strat] = Integrator(prep).integrate(n_iter=6, points=200_000, seed=3, precision="fp32")
+    assert len(prepare_feynman(W.double_box(), strategy="R").sectors) != len(prepare_feynman(W.double_box()).sectors)
+    for n in res["M"].assembled:
+        s = math.hypot(res["M"].assembled_errors[n], res["R"].assembled_errors[n])
+        assert abs(res["M"].assembled[n] - res["R"].assembled[n]) < 4 * s, (n, res["M"].assembled[n], res["R"].assembled[n], s)
