@@ -1,11 +1,13 @@
 """Throughput benchmark of the sector-integrand Monte-Carlo hot path.
 
-One step = one pass of the whole hot path over one workload: every unit
-(sector, eps order) of the one-loop massless box at s = -1, t = -2 (orders
-eps^-2..eps^0, 12 sectors of 3 dims, 32 units) integrated with Vegas,
-10 iterations x 10^6 Philox points per unit (10^7 points per sector per
-order), binary64: point generation, Vegas map, bytecode evaluation,
-reduction, grid refinement and the per-order assembly.
+One step = one pass of the whole hot path over one workload: every
+(sector, eps order) integrand of the one-loop massless box at s = -1, t = -2
+(orders eps^-2..eps^0, 12 sectors of 3 dims, 32 integrands) integrated with
+Vegas, 10 iterations x 10^6 Philox points (10^7 points per sector per order),
+binary64: point generation, Vegas map, bytecode evaluation, reduction, grid
+refinement and the per-order assembly.  By default each sector is one fused
+unit that evaluates all its orders at every point (--fuse 0: one unit per
+sector and order); the metric counts evaluations of (sector, order) integrands.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the oracle (the
 plain CPU restatement of the method) on a bounded sample of the same workload.
@@ -46,18 +48,19 @@ def parse():
     ap.add_argument("--iters", type=int, default=0, help="Vegas iterations per step (0: workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fuse", type=int, default=1, help="1: one unit per sector carrying all its eps orders")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "tta"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
     ap.add_argument("--target", type=float, default=1e-4)
     return ap.parse_args()
 
 
-def prepared(workload):
+def prepared(workload, fuse=False):
     import workloads as W
     from paper_1511_03614_gb300 import prepare_feynman, prepare_direct
     if workload == "stress":
         return prepare_direct(W.stress_suite(), "stress")
-    return prepare_feynman(getattr(W, workload)())
+    return prepare_feynman(getattr(W, workload)(), fuse_orders=bool(fuse))
 
 
 def dist_setup(args):
@@ -191,7 +194,7 @@ def run_ours(args):
     pts, iters, rng = WORKLOADS[args.workload]
     pts = args.points or pts
     iters = args.iters or iters
-    prep = prepared(args.workload)
+    prep = prepared(args.workload, args.fuse)
     lib = N.load()
     peaks = (C.c_double * 7)()
     N.check(lib.fiesta_probe_peaks(peaks, 7))
@@ -222,7 +225,7 @@ def run_ours(args):
         eval_ms += res.stats["eval_ms"]
         launches += res.stats["kernels_launched"]
         eval_launches += res.stats["eval_launches"]
-        points += res.stats["points"]
+        points += res.stats["unit_points"]          # evaluations of (sector, order) integrands
     torch.cuda.synchronize()
     barrier(world)
     ck = clocks.stop()
@@ -269,7 +272,7 @@ def run_ours(args):
             ig.close()
             torch.cuda.synchronize()
             e_times.append(time.perf_counter() - t0)
-            e_points += r.stats["points"]
+            e_points += r.stats["unit_points"]
         et = max_over_ranks(sum(e_times), world)
         e2e = {"value": sum_over_ranks(e_points, world) / et, "unit": "points/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
@@ -293,6 +296,8 @@ def run_ours(args):
                                     "stress": "10000 seeded synthetic integrands, dims 3..8, 2^20 Sobol points"
                                     }[args.workload],
                        "units": len(prep.units), "points_per_unit_per_iter": pts, "iterations": iters,
+                       "fused_orders": bool(args.fuse) and args.workload != "stress",
+                       "results_per_point": sum(u.n_out for u in prep.units) / len(prep.units),
                        "units_fp32": res.stats.get("units_fp32") if res else None,
                        "launch_shape": {"threads": res.stats.get("threads"),
                                         "points_per_thread": res.stats.get("points_per_thread")} if res else None,

@@ -44,6 +44,7 @@ extern "C" {
 
 #define FIESTA_NBINS       128  /* Vegas bins per coordinate */
 #define FIESTA_MAX_DIM       8  /* largest integration dimension */
+#define FIESTA_MAX_OUT       6  /* results (eps orders) of one fused unit */
 
 /*
  * One unit: a straight-line register program (the paper's quadruple list,
@@ -63,6 +64,10 @@ typedef struct {
     uint32_t rng_key;     /* second Philox key word: the unit's point stream */
     const uint32_t *code; /* n_instr words */
     const double *consts; /* n_const values */
+    int32_t n_out;        /* 0 or 1: one result in out_slot; 2..FIESTA_MAX_OUT: a fused unit whose
+                             results are the eps orders order .. order + n_out - 1 (vector-valued
+                             integrand sharing one Vegas grid), in out_slots */
+    const int32_t *out_slots; /* n_out slots (when n_out > 1) */
 } fiesta_program;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  NULL
@@ -103,7 +108,7 @@ typedef struct {
     int32_t order, sector;
     int64_t n_nonfinite;      /* samples whose value was not finite (counted as 0) */
     int32_t precision;        /* FIESTA_FP64 or FIESTA_FP32: how this unit was evaluated */
-    int32_t pad;
+    int32_t unit;             /* unit index (a fused unit gives one record per result) */
     double fp32_error;        /* FIESTA_AUTO: probe estimate of the binary32 error of the mean (else NaN) */
 } fiesta_unit_result;
 
@@ -115,6 +120,7 @@ typedef struct {
     int32_t kernels_launched; /* kernel launches made by this call */
     int32_t eval_launches;    /* of which evaluation-kernel launches */
     int64_t units_fp32;       /* units evaluated in binary32 */
+    int64_t unit_points;      /* points x results: evaluations of (sector, order) integrands */
     int32_t threads[2];       /* block size used for binary64 [0] and binary32 [1] */
     int32_t points_per_thread[2];
 } fiesta_stats;
@@ -137,8 +143,9 @@ int fiesta_load_sectors(fiesta_ctx **out, const fiesta_program *progs, int64_t n
  * order order_lo + k (k < n_orders), the sum over units of that order in
  * value[k] and the mean-square combination sqrt(sum sigma^2) of their errors
  * in error[k] (Sec. 4.3).  value/error are caller-owned host arrays of
- * n_orders doubles.  per_unit (nullable) receives one record per unit of the
- * slice, in unit order; stats (nullable) the timing.  The grids persist in the
+ * n_orders doubles.  per_unit (nullable) receives one record per result of the
+ * slice's units (one per unit, n_out per fused unit), in unit order; stats
+ * (nullable) the timing.  The grids persist in the
  * context between calls (see reset_grid).
  * Errors: FIESTA_E_INVALID, FIESTA_E_CUDA, FIESTA_E_TIMEOUT, FIESTA_E_NONFINITE
  * (results are still written; the message names the first unit affected).
@@ -148,7 +155,7 @@ int fiesta_integrate(fiesta_ctx *ctx, const fiesta_options *opt, double *value, 
 
 /*
  * Evaluate unit `unit` at n points: x is n*dim coordinates in (0,1), row-major,
- * f receives n values.  x and f are both host or both device pointers (the
+ * f receives n*n_out values (row-major: the unit's results per point).  x and f are both host or both device pointers (the
  * library detects which).  precision is FIESTA_FP64 or FIESTA_FP32.  This is
  * the per-point hook, the counterpart of the paper's justEvaluate integrator
  * (Sec. 4.4).  Errors: FIESTA_E_INVALID, FIESTA_E_CUDA.
@@ -157,10 +164,10 @@ int fiesta_eval_batch(fiesta_ctx *ctx, int64_t unit, int32_t precision, const do
                       double *f);
 
 /*
- * Per-iteration results of the last fiesta_integrate call for one unit:
- * mean[i] and var[i] (variance of the mean) for i < n_iter, host arrays.
+ * Per-iteration results of the last fiesta_integrate call for result `out` of
+ * one unit: mean[i] and var[i] (variance of the mean) for i < n_iter, host arrays.
  */
-int fiesta_iterations(fiesta_ctx *ctx, int64_t unit, int32_t n_iter, double *mean, double *var);
+int fiesta_iterations(fiesta_ctx *ctx, int64_t unit, int32_t out, int32_t n_iter, double *mean, double *var);
 
 /*
  * Per-unit binary32 probe (the precision policy of FIESTA_AUTO): evaluate

@@ -19,7 +19,8 @@ FLOW_PARAMS = 4 * (16 * 64 + 64 + 64 * 64 + 64 + 64 * 16 + 16)
 class Program(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_instr", C.c_int32), ("n_const", C.c_int32), ("n_slots", C.c_int32),
                 ("out_slot", C.c_int32), ("order", C.c_int32), ("sector", C.c_int32), ("rng_key", C.c_uint32),
-                ("code", C.POINTER(C.c_uint32)), ("consts", C.POINTER(C.c_double))]
+                ("code", C.POINTER(C.c_uint32)), ("consts", C.POINTER(C.c_double)), ("n_out", C.c_int32),
+                ("out_slots", C.POINTER(C.c_int32))]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -42,13 +43,14 @@ class Options(C.Structure):
 class UnitResult(C.Structure):
     _fields_ = [("value", C.c_double), ("sigma", C.c_double), ("chi2_dof", C.c_double), ("n_points", C.c_int64),
                 ("order", C.c_int32), ("sector", C.c_int32), ("n_nonfinite", C.c_int64), ("precision", C.c_int32),
-                ("pad", C.c_int32), ("fp32_error", C.c_double)]
+                ("unit", C.c_int32), ("fp32_error", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("gpu_ms", C.c_double), ("eval_ms", C.c_double), ("points", C.c_int64),
                 ("points_per_s", C.c_double), ("kernels_launched", C.c_int32), ("eval_launches", C.c_int32),
-                ("units_fp32", C.c_int64), ("threads", C.c_int32 * 2), ("points_per_thread", C.c_int32 * 2)]
+                ("units_fp32", C.c_int64), ("unit_points", C.c_int64), ("threads", C.c_int32 * 2),
+                ("points_per_thread", C.c_int32 * 2)]
 
 
 EXPORTS = {
@@ -57,7 +59,7 @@ EXPORTS = {
     "fiesta_integrate": (C.c_int, [C.c_void_p, C.POINTER(Options), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.c_int32, C.POINTER(UnitResult), C.POINTER(Stats)]),
     "fiesta_eval_batch": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]),
-    "fiesta_iterations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double),
+    "fiesta_iterations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
     "fiesta_precision_probe": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_uint64,
                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]),

@@ -46,11 +46,14 @@ class Integrator:
             cons = np.ascontiguousarray(u.program.consts, dtype=np.float64)
             if cons.size == 0:
                 cons = np.zeros(1)
-            keep += [code, cons]
+            outs = np.ascontiguousarray(u.program.out_slots, dtype=np.int32)
+            keep += [code, cons, outs]
             progs[i] = N.Program(u.dim, code.size, len(u.program.consts), u.program.n_slots, u.program.out_slot,
                                  u.order, u.sector, u.rng_key & 0xFFFFFFFF,
                                  code.ctypes.data_as(C.POINTER(C.c_uint32)),
-                                 cons.ctypes.data_as(C.POINTER(C.c_double)))
+                                 cons.ctypes.data_as(C.POINTER(C.c_double)), int(u.n_out),
+                                 outs.ctypes.data_as(C.POINTER(C.c_int32)))
+        self._keep = keep
         alloc = None
         if torch_alloc:
             dev = self.device
@@ -70,15 +73,14 @@ class Integrator:
             N.check(self.lib.fiesta_load_sectors(C.byref(ctx), progs, n, C.byref(alloc) if alloc else None,
                                                  C.c_void_p(self.stream.cuda_stream)))
         self.ctx = ctx
-        del keep
 
     # ------------------------------------------------------------------ integrate
     def integrate(self, n_iter=10, points=100_000, seed=1, rng="philox", precision="fp64", adapt=True,
                   alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
                   iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
                   probe_points=0, fp32_budget=0.0):
-        orders = [u.order for u in self.prep.units]
-        lo, hi = min(orders), max(orders)
+        lo = min(u.order for u in self.prep.units)
+        hi = max(u.order + u.n_out - 1 for u in self.prep.units)
         nord = hi - lo + 1
         b, e = (0, len(self.prep.units)) if units is None else units
         opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(adapt), int(points),
@@ -87,7 +89,7 @@ class Integrator:
                         int(points_per_thread), int(probe_points), float(fp32_budget))
         val = (C.c_double * nord)()
         err = (C.c_double * nord)()
-        per = (N.UnitResult * (e - b))()
+        per = (N.UnitResult * sum(u.n_out for u in self.prep.units[b:e]))()
         st = N.Stats()
         with self._torch.cuda.device(self.device):
             rc = self.lib.fiesta_integrate(self.ctx, C.byref(opt), val, err, nord, per, C.byref(st))
@@ -97,10 +99,11 @@ class Integrator:
         errors = {lo + k: err[k] for k in range(nord)}
         pu = [dict(value=r.value, sigma=r.sigma, chi2_dof=r.chi2_dof, n_points=r.n_points, order=r.order,
                    sector=r.sector, n_nonfinite=r.n_nonfinite, precision=("fp64", "fp32")[r.precision],
-                   fp32_error=r.fp32_error) for r in per]
+                   unit=r.unit, fp32_error=r.fp32_error) for r in per]
         stats = dict(gpu_ms=st.gpu_ms, eval_ms=st.eval_ms, points=st.points, points_per_s=st.points_per_s,
                      kernels_launched=st.kernels_launched, eval_launches=st.eval_launches,
-                     units_fp32=st.units_fp32, threads=tuple(st.threads), points_per_thread=tuple(st.points_per_thread))
+                     units_fp32=st.units_fp32, unit_points=st.unit_points, threads=tuple(st.threads),
+                     points_per_thread=tuple(st.points_per_thread))
         res = Result(values, errors, pu, stats)
         if assemble_result and units is None:
             res.assembled, res.assembled_errors = assemble(self.prep, values, errors)
@@ -108,17 +111,20 @@ class Integrator:
 
     # ------------------------------------------------------------------ per point
     def eval_batch(self, unit, x, precision="fp64"):
-        """f at points x (n, dim): a torch CUDA tensor (result on the device) or a host array."""
+        """f at points x (n, dim): a torch CUDA tensor (result on the device) or a host array.
+        A fused unit returns (n, n_out)."""
         torch = self._torch
+        nout = self.prep.units[unit].n_out
+        shape = (x.shape[0],) if nout == 1 else (x.shape[0], nout)
         if isinstance(x, torch.Tensor) and x.is_cuda:
             x = x.to(torch.float64).contiguous()
-            f = torch.empty(x.shape[0], dtype=torch.float64, device=x.device)
+            f = torch.empty(shape, dtype=torch.float64, device=x.device)
             with torch.cuda.device(self.device):
                 N.check(self.lib.fiesta_eval_batch(self.ctx, int(unit), N.PRECISION[precision],
                                                    C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(f.data_ptr())))
             return f
         x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
-        f = np.empty(x.shape[0])
+        f = np.empty(shape)
         with torch.cuda.device(self.device):
             N.check(self.lib.fiesta_eval_batch(self.ctx, int(unit), N.PRECISION[precision],
                                                x.ctypes.data_as(C.c_void_p), x.shape[0], f.ctypes.data_as(C.c_void_p)))
@@ -187,10 +193,10 @@ class Integrator:
                                            g.ctypes.data_as(C.POINTER(C.c_float))))
         return dict(x=x, logq=lq, f=f, logq_train=lqt, loss=loss[0], grad=g)
 
-    def iterations(self, unit, n_iter):
+    def iterations(self, unit, n_iter, out=0):
         m = (C.c_double * n_iter)()
         v = (C.c_double * n_iter)()
-        N.check(self.lib.fiesta_iterations(self.ctx, int(unit), int(n_iter), m, v))
+        N.check(self.lib.fiesta_iterations(self.ctx, int(unit), int(out), int(n_iter), m, v))
         return np.array(m[:]), np.array(v[:])
 
     def get_grid(self, unit):
@@ -237,7 +243,8 @@ def save_checkpoint(path, integ, state):
     import struct
     import zlib
     grids = [integ.get_grid(k) for k in range(len(integ.prep.units))]
-    header = json.dumps({"n_units": len(grids), "dims": [g.shape[0] for g in grids], "it": state["it"],
+    header = json.dumps({"n_units": len(grids), "n_rec": len(state["sw"]), "dims": [g.shape[0] for g in grids],
+                         "it": state["it"],
                          "seed": state["seed"], "precision": state["precision"], "rng": state["rng"],
                          "points": state["points"], "gpu_ms": state["gpu_ms"],
                          "points_done": state["points_done"]}).encode()
@@ -268,7 +275,8 @@ def load_checkpoint(path, integ=None):
     h = json.loads(body[4:4 + hl].decode())
     data = np.frombuffer(body[4 + hl:], dtype="<f8")
     n = h["n_units"]
-    need = sum(d * (N.NBINS + 1) for d in h["dims"]) + 2 * n
+    nr = h.get("n_rec", n)
+    need = sum(d * (N.NBINS + 1) for d in h["dims"]) + 2 * nr
     if data.size != need:
         raise ValueError("checkpoint payload has the wrong size")
     grids = []
@@ -276,8 +284,8 @@ def load_checkpoint(path, integ=None):
     for d in h["dims"]:
         grids.append(data[off:off + d * (N.NBINS + 1)].reshape(d, N.NBINS + 1))
         off += d * (N.NBINS + 1)
-    sw = data[off:off + n].copy()
-    swi = data[off + n:off + 2 * n].copy()
+    sw = data[off:off + nr].copy()
+    swi = data[off + nr:off + 2 * nr].copy()
     if integ is not None:
         if len(integ.prep.units) != n or any(u.dim != d for u, d in zip(integ.prep.units, h["dims"])):
             raise ValueError("checkpoint does not match these units")
@@ -303,7 +311,8 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
     iterations and the final values and errors.
     """
     prep = integ.prep
-    nu = len(prep.units)
+    recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
+    nu = len(recs)
     sw = np.zeros(nu)
     swi = np.zeros(nu)
     gpu_ms = 0.0
@@ -318,9 +327,9 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
         r = integ.integrate(n_iter=iters_per_call, points=points, seed=seed, rng=rng, precision=precision,
                             adapt=2, reset_grid=(it == 0), iter_offset=it, assemble_result=False)
         gpu_ms += r.stats["gpu_ms"]
-        points_done += r.stats["points"]
-        for k in range(nu):
-            m, v = integ.iterations(k, iters_per_call)
+        points_done += r.stats["unit_points"]
+        for k, (unit, o) in enumerate(recs):
+            m, v = integ.iterations(unit, iters_per_call, o)
             for j in range(iters_per_call):
                 if it + j < skip_first:
                     continue
@@ -336,9 +345,10 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
         val = swi / sw
         sig = np.sqrt(1.0 / sw)
         values, errors = {}, {}
-        for k, u in enumerate(prep.units):
-            values[u.order] = values.get(u.order, 0.0) + val[k]
-            errors[u.order] = errors.get(u.order, 0.0) + sig[k] ** 2
+        for k, (unit, o) in enumerate(recs):
+            K = prep.units[unit].order + o
+            values[K] = values.get(K, 0.0) + val[k]
+            errors[K] = errors.get(K, 0.0) + sig[k] ** 2
         errors = {K: math.sqrt(e) for K, e in errors.items()}
         R, E = assemble(prep, values, errors)
         big = max(abs(v) for v in R.values())

@@ -54,9 +54,14 @@ class Program:
     code: np.ndarray        # uint32
     consts: np.ndarray      # float64
     n_slots: int
-    out_slot: int
+    out_slot: int           # slot of the (first) result
     dim: int
     counts: dict            # opcode name -> number of instructions
+    out_slots: tuple = ()   # slots of all results (several for a fused multi-order unit)
+
+    def __post_init__(self):
+        if not self.out_slots:
+            self.out_slots = (self.out_slot,)
 
     def flops(self):
         """Arithmetic operations per point: ADD/SUB/MUL/NEG/ADDC/MULC = 1, MAC/MACC = 2,
@@ -66,11 +71,92 @@ class Program:
             2 * (c.get("MAC", 0) + c.get("MACC", 0))
 
 
+def _args(n):
+    if n[0] in ("add", "sub", "mul", "div"):
+        return (n[1], n[2])
+    if n[0] == "fma":
+        return (n[1], n[2], n[3])
+    if n[0] in ("neg", "log", "inv", "powi"):
+        return (n[1],)
+    return ()
+
+
+def _schedule(nodes, live, outs):
+    """Order the live nodes for low register pressure: greedy list scheduling that
+    always emits, among the nodes whose operands are available, one that frees the
+    most slots (operands at their last use) net of the slot it occupies; ties go to
+    the node created first.  Constants take no slot of their own here and are placed
+    just before their first user."""
+    import heapq
+    outset = set(outs)
+    preds, users = {}, {i: set() for i in live}
+    for i in live:
+        p = set(a for a in _args(nodes[i]) if nodes[a][0] != "c")
+        preds[i] = p
+        for a in p:
+            users[a].add(i)
+    remaining = {i: len(users[i]) for i in live}
+    waiting = {i: len(preds[i]) for i in live}
+
+    def score(i):
+        freed = sum(1 for a in preds[i] if remaining[a] == 1 and a not in outset)
+        occupies = 1 if (users[i] or i in outset) else 0
+        return freed - occupies
+
+    heap = []
+    for i in live:
+        if nodes[i][0] != "c" and waiting[i] == 0:
+            heapq.heappush(heap, (-score(i), i))
+    order = []
+    done = set()
+    while heap:
+        s, i = heapq.heappop(heap)
+        if i in done:
+            continue
+        cur = -score(i)
+        if cur != s:                       # stale priority: re-queue with the current one
+            heapq.heappush(heap, (cur, i))
+            continue
+        done.add(i)
+        order.append(i)
+        touched = set()
+        for a in preds[i]:
+            remaining[a] -= 1
+            touched |= users[a]
+        for u in users[i]:
+            waiting[u] -= 1
+            if waiting[u] == 0:
+                heapq.heappush(heap, (-score(u), u))
+        for u in touched:                  # their scores may have improved
+            if u not in done and waiting[u] == 0:
+                heapq.heappush(heap, (-score(u), u))
+    # constants just before their first user
+    consts = [i for i in live if nodes[i][0] == "c"]
+    first_use = {}
+    pos = {i: k for k, i in enumerate(order)}
+    for i in order:
+        for a in _args(nodes[i]):
+            if nodes[a][0] == "c" and a not in first_use:
+                first_use[a] = pos[i]
+    out = []
+    by_pos = {}
+    for cidx in consts:
+        by_pos.setdefault(first_use.get(cidx, len(order)), []).append(cidx)
+    for k, i in enumerate(order):
+        out.extend(by_pos.get(k, []))
+        out.append(i)
+    out.extend(by_pos.get(len(order), []))
+    return out
+
+
 def emit(graph, out, dim):
-    """Lower the nodes reachable from ``out`` to a Program (linear-scan slot allocation)."""
+    """Lower the nodes reachable from ``out`` (one node or a list of result nodes) to a
+    Program (linear-scan slot allocation); results stay live to the end."""
+    outs = list(out) if isinstance(out, (list, tuple)) else [out]
+    out = outs[0]
     nodes = graph.nodes
     live = set()
-    stack = [out]
+    stack = list(outs)
     while stack:
         i = stack.pop()
         if i in live:
@@ -83,7 +169,7 @@ def emit(graph, out, dim):
             stack += [n[1], n[2], n[3]]
         elif n[0] in ("neg", "log", "inv", "powi"):
             stack.append(n[1])
-    order = sorted(live)
+    order = _schedule(nodes, live, outs)
 
     consts = []
     cidx = {}
@@ -125,7 +211,8 @@ def emit(graph, out, dim):
                 continue
             uses.setdefault(a, []).append(pos)
     last = {a: max(p) for a, p in uses.items()}
-    last[out] = len(order)
+    for o in outs:
+        last[o] = len(order)
 
     code = []
     counts = {}
@@ -149,7 +236,7 @@ def emit(graph, out, dim):
     for pos, i in enumerate(order):
         n = nodes[i]
         kind = n[0]
-        if kind == "c" and i not in uses and i != out:
+        if kind == "c" and i not in uses and i not in outs:
             continue                      # only used folded
         # release operands whose last use is here (their slots may be reused by dst)
         args = ()
@@ -209,7 +296,7 @@ def emit(graph, out, dim):
     if len(consts) > MAX_CONST:
         raise OverflowError("too many constants")
     prog = Program(np.array(code, dtype=np.uint32), np.array(consts, dtype=np.float64),
-                   max(n_slots, 1), slot[out], dim, counts)
+                   max(n_slots, 1), slot[out], dim, counts, tuple(slot[o] for o in outs))
     validate(prog)
     return prog
 
@@ -257,5 +344,6 @@ def validate(prog):
             if r not in written:
                 raise ValueError(f"slot {r} read before written at {pc}")
         written.add(d)
-    if prog.out_slot not in written:
-        raise ValueError("output slot never written")
+    for o in prog.out_slots:
+        if o not in written:
+            raise ValueError("output slot never written")

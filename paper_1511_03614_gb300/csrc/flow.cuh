@@ -724,6 +724,9 @@ int fiesta_flow_sample(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int6
         return fail(FIESTA_E_INVALID, "fiesta_flow_sample: bad unit range, point count or keep");
     if (precision != FIESTA_FP64 && precision != FIESTA_FP32)
         return fail(FIESTA_E_INVALID, "fiesta_flow_sample: precision must be FP64 or FP32");
+    for (int64_t k = unit_begin; k < unit_end; ++k)
+        if (c->units[k].n_out > 1)
+            return fail(FIESTA_E_INVALID, "fiesta_flow_sample: units with several results are not supported");
     int r = flow_alloc(c, keep);
     if (r) return r;
     FlowState *F = c->flow;
@@ -764,7 +767,8 @@ int fiesta_flow_sample(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int6
     if (r) return r;
     const unsigned rb = (unsigned)((nu * 32 + 255) / 256);
     k_reduce<<<rb, 256, 0, c->stream>>>(c->d_part_sv, c->d_part_sv2, c->d_part_bad, nu, bpu, points, 1, 0,
-                                         c->d_iter_mean, c->d_iter_var, c->d_unit_bad);
+                                         c->d_iter_mean, c->d_iter_var, c->d_unit_bad, c->d_units, nullptr,
+                                         unit_begin, 1);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(e1, c->stream));
     std::vector<unsigned long long> bad(nu);

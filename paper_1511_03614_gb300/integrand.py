@@ -218,3 +218,16 @@ def unit_graph(sec, K):
 
 def min_order(sec):
     return -len(singular(sec))
+
+
+def sector_graph(sec, orders):
+    """(Graph, result nodes) with the integrands of every order in ``orders`` of one
+    sector in a single graph (shared subexpressions); identically-zero orders give a
+    constant 0 result."""
+    g = Graph()
+    ev = _SectorEval(g, sec)
+    outs = []
+    for K in orders:
+        node = ev.unit(K) if K >= -len(ev.S) else None
+        outs.append(g.c(0.0) if node is None else node)
+    return g, outs

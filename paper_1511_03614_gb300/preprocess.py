@@ -21,10 +21,11 @@ from .symanzik import symanzik
 @dataclasses.dataclass
 class Unit:
     sector: int
-    order: int
+    order: int                # eps order of the (first) result
     dim: int
     program: B.Program
     rng_key: int
+    n_out: int = 1            # results: orders order .. order + n_out - 1 (fused multi-order unit)
 
 
 @dataclasses.dataclass
@@ -54,7 +55,29 @@ def _units_for(sectors, orders_of):
     return units
 
 
-def prepare_feynman(problem, strategy="M"):
+MAX_OUT = 6
+
+
+def _fused_units(sectors, orders_of):
+    """One unit per sector whose program returns every eps order of the sector: the
+    orders share the polynomial values, logarithms and corner terms (one evaluation
+    of U, F and the subtraction corners per point instead of one per order)."""
+    units = []
+    for si, sec in enumerate(sectors):
+        Ks = list(orders_of(sec))
+        if not Ks:
+            continue
+        if len(Ks) > MAX_OUT:
+            raise ValueError(f"a fused unit holds at most {MAX_OUT} orders")
+        g, outs = I.sector_graph(sec, Ks)
+        prog = B.emit(g, outs, len(sec.variables))
+        units.append(Unit(si, Ks[0], len(sec.variables), prog, len(units), n_out=len(Ks)))
+    return units
+
+
+def prepare_feynman(problem, strategy="M", fuse_orders=False):
+    """Units of a Feynman integral; with ``fuse_orders`` one unit per sector carries all
+    its eps orders (a vector-valued integrand with one Vegas grid)."""
     U, F = symanzik(problem)
     n = len(problem.propagators)
     L = len(problem.loop_momenta)
@@ -62,7 +85,8 @@ def prepare_feynman(problem, strategy="M"):
     kmin = min(I.min_order(s) for s in secs)
     q0, _ = PF.series(problem.indices, L, 0)
     khi = problem.order + q0
-    units = _units_for(secs, lambda s: range(max(kmin, I.min_order(s)), khi + 1))
+    orders_of = lambda s: range(max(kmin, I.min_order(s)), khi + 1)
+    units = (_fused_units if fuse_orders else _units_for)(secs, orders_of)
     pre = PF.series(problem.indices, L, problem.order - kmin)
     return Prepared(problem.name, units, pre, tuple(range(kmin, khi + 1)),
                     tuple(range(kmin - pre[0], problem.order + 1)), secs)
@@ -91,21 +115,28 @@ def prepare_direct(problems, name="direct"):
     return Prepared(name, units, (0, [1.0]), orders, orders, secs)
 
 
-def assemble(prep, values, errors):
-    """Step a6: R_n = sum_m c_m I_{n-m}, sigma_n^2 = sum_m c_m^2 sigma_{n-m}^2 (independent units).
+def assemble(prep, values, errors, correlated=None):
+    """Step a6: R_n = sum_m c_m I_{n-m}.
 
+    With one unit per (sector, order) the I_K are independent and
+    sigma_n^2 = sum_m c_m^2 sigma_{n-m}^2.  Fused units evaluate all orders of a
+    sector at the same points, so I_K of different K are correlated; then the
+    bound sigma_n <= sum_m |c_m| sigma_{n-m}, valid for any correlation, is used.
     ``values``/``errors`` map eps orders of the parametric integral to sums over
-    sectors (errors already combined in the mean-square norm, Sec. 4.3).
+    sectors (errors combined in the mean-square norm, Sec. 4.3).
     """
+    if correlated is None:
+        correlated = any(getattr(u, "n_out", 1) > 1 for u in prep.units)
     q, c = prep.prefactor
     R, E = {}, {}
     for n in prep.out_orders:
-        v, e2 = 0.0, 0.0
+        v, e2, e1 = 0.0, 0.0, 0.0
         for i, ci in enumerate(c):
             K = n - (i - q)
             if K in values:
                 v += ci * values[K]
                 e2 += (ci * errors[K]) ** 2
+                e1 += abs(ci) * errors[K]
         R[n] = v
-        E[n] = math.sqrt(e2)
+        E[n] = e1 if correlated else math.sqrt(e2)
     return R, E

@@ -48,4 +48,6 @@ def run(prog, X, dtype=np.float64):
                 s[d] = 1.0 / s[a]
             elif name == "MOV":
                 s[d] = s[a]
+    if len(prog.out_slots) > 1:
+        return np.stack([s[o].copy() for o in prog.out_slots], axis=1)
     return s[prog.out_slot].copy()

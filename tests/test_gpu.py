@@ -328,3 +328,40 @@ def test_double_box_strategy_invariance():
     for n in res["M"].assembled:
         s = math.hypot(res["M"].assembled_errors[n], res["R"].assembled_errors[n])
         assert abs(res["M"].assembled[n] - res["R"].assembled[n]) < 4 * s, (n, res["M"].assembled[n], res["R"].assembled[n], s)
+
+
+def test_fused_units_match_oracle_and_closed_form():
+    """Fused multi-order units: per point and per same-point iteration against the
+    oracle's per-order units, and the box closed form."""
+    need_gpu()
+    import workloads as W
+    from paper_1511_03614_gb300 import prepare_feynman, Integrator
+    prep = prepare_feynman(W.box(), fuse_orders=True)
+    _, orc = feynman("box")
+    by = {(u.sector, u.order): u for u in orc.units}
+    integ = Integrator(prep)
+    rng = np.random.default_rng(21)
+    for i, u in enumerate(prep.units):
+        X = sample_points(u.dim, rng, 32)
+        f = integ.eval_batch(i, X)
+        for k in range(u.n_out):
+            o = by[(u.sector, u.order + k)]
+            ref = _ref(o, X)
+            assert np.all(np.abs(f[:, k] - ref) <= 1e-12 * np.maximum(P.magnitude_numpy(o, X), 1e-300))
+    N = 20000
+    integ.integrate(n_iter=1, points=N, seed=9, adapt=False)
+    for i, u in enumerate(prep.units):
+        for k in range(u.n_out):
+            o = by[(u.sector, u.order + k)]
+            m, _ = integ.iterations(i, 1, k)
+            r = V.integrate_unit(o.f_numpy, o.dim, 1, N, 9, u.rng_key, adapt=False)
+            U = V.philox.uniforms(9, u.rng_key, 0, 0, N, o.dim)
+            X, J, _ = V.vegas_map(r.grids[0], U)
+            absum = np.mean(np.abs(o.f_numpy(X) * J))
+            assert abs(m[0] - r.iters[0][0]) <= 1e-11 * absum
+    res = integ.integrate(n_iter=10, points=1_000_000, seed=2)
+    assert len(res.per_unit) == sum(u.n_out for u in prep.units)
+    exact = {-2: 2.0, -1: -math.log(2.0), 0: -2 * math.pi ** 2 / 3}
+    for n, v in exact.items():
+        s = res.assembled_errors[n]
+        assert abs(res.assembled[n] - v) < 4 * s, (n, res.assembled[n], v, s)

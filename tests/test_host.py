@@ -121,3 +121,26 @@ def test_load_rejects_invalid_program_without_gpu():
     ctx = C.c_void_p()
     rc = lib.fiesta_load_sectors(C.byref(ctx), progs, 1, None, None)
     assert rc == -1 and b"read before written" in lib.fiesta_last_error()
+
+
+@pytest.mark.parametrize("name", ["bubble", "box", "double_box"])
+def test_fused_programs_match_oracle(name):
+    """A fused unit's results are the oracle's per-order integrands of its sector."""
+    prob = getattr(W, name)()
+    prep = prepare_feynman(prob, fuse_orders=True)
+    orc = P.feynman_problem(prob)
+    by = {(u.sector, u.order): u for u in orc.units}
+    assert sum(u.n_out for u in prep.units) >= len(orc.units)
+    rng = np.random.default_rng(5)
+    idx = range(len(prep.units)) if len(prep.units) < 20 else rng.choice(len(prep.units), 12, replace=False)
+    for i in idx:
+        u = prep.units[i]
+        X = rng.uniform(0.05, 1.0, size=(24, u.dim))
+        Fv = run(u.program, X)
+        Fv = Fv[:, None] if Fv.ndim == 1 else Fv
+        for k in range(u.n_out):
+            o = by.get((u.sector, u.order + k))
+            if o is None:
+                assert np.all(Fv[:, k] == 0)
+                continue
+            assert np.all(np.abs(Fv[:, k] - o.f_numpy(X)) <= 1e-13 * P.magnitude_numpy(o, X))
