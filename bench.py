@@ -243,8 +243,14 @@ def run_ours(args):
     achieved = 2.0 * slots_per_launch / avg_eval_s * 1e-12          # FMA-equivalent TFLOP/s
     peak_meas = peaks[0]
     nominal = 1.25
+    # DRAM bytes per launch of the evaluation kernel from an ncu capture (read + write); the
+    # kernel stages programs, constants and grids in shared memory, so this does not grow
+    # with the number of points
+    traffic = 110336 if (args.workload == "box" and args.precision == "fp64" and args.fuse) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "TFLOP/s",
-                "frac": achieved / peak_meas, "traffic": None,
+                "frac": achieved / peak_meas, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_eval<double, Philox, 6> "
+                                  "on the fused box (12 units x 2e5 points, one launch)" if traffic else None,
                 "kernel": "k_eval", "work": "FMA-equivalent pipe slots x 2 per launch (log/div weighted by "
                 "measured cost)", "peak_source": "measured in-process (fiesta_probe_peaks)",
                 "nominal_fp64_tflops": nominal,
