@@ -97,7 +97,10 @@ typedef struct {
     int32_t points_per_thread;/* points per thread per work item; 0 = autotuned */
     int64_t probe_points;     /* FIESTA_AUTO: probe points per unit (0: 16384) */
     double fp32_budget;       /* FIESTA_AUTO: largest relative error of a unit's mean accepted in binary32 (0: 1e-6) */
-    int32_t reserved[4];
+    int32_t no_graph;         /* nonzero: launch directly instead of replaying the iteration loop as a
+                                 CUDA graph (captured on the first call, reused while the call's
+                                 parameters are unchanged) */
+    int32_t reserved[3];
 } fiesta_options;
 
 typedef struct {

@@ -365,3 +365,16 @@ def test_fused_units_match_oracle_and_closed_form():
     for n, v in exact.items():
         s = res.assembled_errors[n]
         assert abs(res.assembled[n] - v) < 4 * s, (n, res.assembled[n], v, s)
+
+
+def test_graph_replay_matches_direct_launches():
+    """The iteration loop replayed as a CUDA graph gives what direct launches give."""
+    need_gpu()
+    integ = integrator("box")
+    kw = dict(n_iter=3, points=100_000, seed=31, adapt=False)
+    a = integ.integrate(graph=False, **kw)
+    b = integ.integrate(graph=True, **kw)       # captured
+    c = integ.integrate(graph=True, **kw)       # replayed
+    for x, y, z in zip(a.per_unit, b.per_unit, c.per_unit):
+        assert x["value"] == y["value"] == z["value"] and x["sigma"] == y["sigma"] == z["sigma"]
+    assert b.stats["eval_ms"] > 0 and c.stats["eval_ms"] > 0
