@@ -26,6 +26,7 @@ class Unit:
     order: int                  # eps order K of the parametric integral
     variables: tuple            # original indices; dimension i of the cube <-> variables[i]
     expr: object                # sympy expression in t-symbols
+    complex: bool = False       # deformed contour: complex values
     _np: object = None
     _mp: object = None
 
@@ -34,14 +35,17 @@ class Unit:
         return len(self.variables)
 
     def f_numpy(self, X):
-        """Evaluate in float64 at points X of shape (n, dim)."""
+        """Evaluate in float64 (complex128 for a deformed contour) at points X of shape (n, dim)."""
         if self._np is None:
             syms = [S.tsym(j) for j in self.variables]
             self._np = sp.lambdify(syms, self.expr, modules="numpy")
         cols = [X[:, i] for i in range(self.dim)]
+        if self.complex:
+            cols = [c.astype(np.complex128) for c in cols]
         with np.errstate(all="ignore"):
             v = self._np(*cols)
-        return np.broadcast_to(np.asarray(v, dtype=np.float64), (X.shape[0],)).copy()
+        dt = np.complex128 if self.complex else np.float64
+        return np.broadcast_to(np.asarray(v, dtype=dt), (X.shape[0],)).copy()
 
     def f_mp(self, x, dps=50):
         """Evaluate at one point with mpmath at ``dps`` digits (x given as exact binary64)."""
@@ -62,7 +66,10 @@ class Problem:
     out_orders: tuple         # orders n of the final result
 
 
-def feynman_problem(problem, strategy="M"):
+def feynman_problem(problem, strategy="M", lam=None):
+    """Units of a Feynman integral.  ``lam``: a contour-deformation parameter per
+    sector (callable sector -> lam or None, or one number for every sector whose F
+    has a coefficient that is not positive)."""
     U, F, xs = symanzik(problem)
     L = len(problem.loop_momenta)
     prim = S.primary_sectors(U, F, xs, problem.indices, L)
@@ -73,10 +80,16 @@ def feynman_problem(problem, strategy="M"):
     pre = prefactor_series(problem.indices, L, problem.order - kmin)
     units = []
     for i, s in enumerate(secs):
+        if callable(lam):
+            ls = lam(s)
+        elif lam is not None and any(c <= 0 for c in s.polys[-1][0].coeffs()):
+            ls = lam
+        else:
+            ls = None
         for K in range(max(kmin, S.min_order(s)), khi + 1):
-            e = S.unit_integrand(s, K)
+            e = S.unit_integrand(s, K, ls)
             if e != 0:
-                units.append(Unit(i, K, s.variables, e))
+                units.append(Unit(i, K, s.variables, e, complex=ls is not None))
     int_orders = tuple(range(kmin, khi + 1))
     out_orders = tuple(range(kmin - pre[0], problem.order + 1))
     return Problem(problem.name, secs, units, pre, int_orders, out_orders)

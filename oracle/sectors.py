@@ -226,11 +226,35 @@ def min_order(sec: Sector):
     return -len(singular_vars(sec))
 
 
-def unit_integrand(sec: Sector, K: int):
+def deformation(sec: Sector, lam, poly_index=-1):
+    """Contour deformation of the sector variables (physical kinematics).
+
+    With F the sector's polynomial ``sec.polys[poly_index]``, z_j = t_j - i lam
+    t_j (1 - t_j) dF/dt_j; the deformation vanishes on the faces t_j = 0, 1, so the
+    integral over the cube is unchanged (Cauchy) while Im F(z) <= 0 for small lam
+    enforces the F - i0 prescription of the propagators (Sec. 1, Eq. 1).  Returns
+    (z, w, detJ): z_j, w_j = z_j / t_j = 1 - i lam (1 - t_j) dF/dt_j, det dz/dt.
+    """
+    t = [tsym(j) for j in sec.variables]
+    F = sec.polys[poly_index][0].as_expr()
+    z, w = {}, {}
+    for j, tj in zip(sec.variables, t):
+        dF = sp.diff(F, tj)
+        w[j] = 1 - sp.I * lam * (1 - tj) * dF
+        z[j] = tj * w[j]
+    J = sp.Matrix([[sp.diff(z[j], tk) for tk in t] for j in sec.variables])
+    return z, w, sp.expand(J.det())
+
+
+def unit_integrand(sec: Sector, K: int, lam=None):
     """The sympy expression of the eps^K coefficient of the subtracted sector integrand.
 
     Variables not integrated analytically keep their t-dependence; variables whose
     pole term was taken appear not at all (the integrand is constant along them).
+    With ``lam`` the contour is deformed (``deformation``): the integrand
+    prod_j z_j^{c_j + b_j eps} G(z) det J equals prod_j t_j^{c_j + b_j eps} times
+    [prod_j w_j^{c_j + b_j eps} G(z) det J], and the bracket takes the place of G
+    in the subtraction and the expansion; the result is complex.
     """
     S = singular_vars(sec)
     if K < -len(S):
@@ -239,13 +263,26 @@ def unit_integrand(sec: Sector, K: int):
     # G_n = prod P^{a0} * extra logs * L^n / n!,  L = sum a1 log P
     G0 = sp.Integer(1)
     Lsum = sp.Integer(0)
+    if lam is not None:
+        z, w, detJ = deformation(sec, lam)
+        zsub = {t[j]: z[j] for j in sec.variables}
+        G0 = detJ
+        for j in sec.variables:
+            c, b = sec.mono[j]
+            G0 = G0 * w[j] ** c
+            if b:
+                Lsum = Lsum + b * sp.log(w[j])
+    else:
+        zsub = {}
     for P, (a0, a1) in sec.polys:
-        e = P.as_expr()
+        e = P.as_expr().subs(zsub, simultaneous=True) if zsub else P.as_expr()
         G0 = G0 * e ** a0
         if a1:
             Lsum = Lsum + a1 * sp.log(e)
     for idx, power in sec.log_factor:
-        G0 = G0 * sp.log(sec.polys[idx][0].as_expr()) ** power
+        e = sec.polys[idx][0].as_expr()
+        e = e.subs(zsub, simultaneous=True) if zsub else e
+        G0 = G0 * sp.log(e) ** power
     # highest eps power any factor may need: K plus the poles it can multiply
     nmax = K + len(S)
     Gn = [G0 * Lsum ** n / math.factorial(n) for n in range(nmax + 1)]

@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "FeynmanProblem", "DirectProblem", "DirectFactor",
-    "bubble", "box", "box_paper_example", "double_box", "double_box_alt_routing",
+    "bubble", "box", "box_physical", "box_paper_example", "double_box", "double_box_alt_routing",
     "stress_suite", "STRESS_SEED",
 ]
 
@@ -85,6 +85,12 @@ def box(order: int = 0, S=1, T=2) -> FeynmanProblem:
         indices=(1, 1, 1, 1),
         kinematics=_box_kin(S, T),
         order=order)
+
+
+def box_physical(order: int = 0, s=3, t=-1) -> FeynmanProblem:
+    """The massless box at a physical point s > 0, t < 0 (F changes sign: contour deformation)."""
+    p = box(order=order, S=-s, T=-t)
+    return dataclasses.replace(p, name="box_physical")
 
 
 def box_paper_example() -> FeynmanProblem:
