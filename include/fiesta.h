@@ -49,8 +49,8 @@ extern "C" {
 /*
  * One unit: a straight-line register program (the paper's quadruple list,
  * Sec. 2.1) plus its constants.  Instruction word: op | dst<<8 | a<<16 | b<<24,
- * opcodes 1..15 as documented in the Python package's bytecode module
- * (LDX LDC ADD SUB MUL DIV NEG MAC ADDC MULC MACC POWI LOG INV MOV).
+ * opcodes 1..16 as documented in the Python package's bytecode module
+ * (LDX LDC ADD SUB MUL DIV NEG MAC ADDC MULC MACC POWI LOG INV MOV ATAN2).
  * code/consts are host pointers, read during fiesta_load_sectors only.
  */
 typedef struct {
@@ -68,6 +68,8 @@ typedef struct {
                              results are the eps orders order .. order + n_out - 1 (vector-valued
                              integrand sharing one Vegas grid), in out_slots */
     const int32_t *out_slots; /* n_out slots (when n_out > 1) */
+    int32_t cplx;         /* nonzero: a contour-deformed unit whose results are (re, im) pairs,
+                             result 2k + p being part p of eps order order + k */
 } fiesta_program;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  NULL
@@ -112,6 +114,8 @@ typedef struct {
     int64_t n_nonfinite;      /* samples whose value was not finite (counted as 0) */
     int32_t precision;        /* FIESTA_FP64 or FIESTA_FP32: how this unit was evaluated */
     int32_t unit;             /* unit index (a fused unit gives one record per result) */
+    int32_t part;             /* complex units: 0 real part, 1 imaginary part */
+    int32_t pad;
     double fp32_error;        /* FIESTA_AUTO: probe estimate of the binary32 error of the mean (else NaN) */
 } fiesta_unit_result;
 
@@ -143,7 +147,8 @@ int fiesta_load_sectors(fiesta_ctx **out, const fiesta_program *progs, int64_t n
 
 /*
  * Integrate every unit of the slice with Vegas (Sec. 4.4) and return, per eps
- * order order_lo + k (k < n_orders), the sum over units of that order in
+ * order order_lo + k (k < n_orders), the sum over units of that order (real
+ * parts; imaginary parts of complex units are in the per-unit records) in
  * value[k] and the mean-square combination sqrt(sum sigma^2) of their errors
  * in error[k] (Sec. 4.3).  value/error are caller-owned host arrays of
  * n_orders doubles.  per_unit (nullable) receives one record per result of the

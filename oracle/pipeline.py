@@ -164,4 +164,4 @@ def magnitude_numpy(unit, X):
         unit._abs = sp.lambdify(syms, _absify(unit.expr), modules="numpy")
     with np.errstate(all="ignore"):
         v = unit._abs(*[X[:, i] for i in range(unit.dim)])
-    return np.broadcast_to(np.asarray(v, dtype=np.float64), (X.shape[0],)).copy()
+    return np.broadcast_to(np.abs(np.asarray(v)).astype(np.float64), (X.shape[0],)).copy()

@@ -20,7 +20,7 @@ class Program(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_instr", C.c_int32), ("n_const", C.c_int32), ("n_slots", C.c_int32),
                 ("out_slot", C.c_int32), ("order", C.c_int32), ("sector", C.c_int32), ("rng_key", C.c_uint32),
                 ("code", C.POINTER(C.c_uint32)), ("consts", C.POINTER(C.c_double)), ("n_out", C.c_int32),
-                ("out_slots", C.POINTER(C.c_int32))]
+                ("out_slots", C.POINTER(C.c_int32)), ("cplx", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -44,7 +44,7 @@ class Options(C.Structure):
 class UnitResult(C.Structure):
     _fields_ = [("value", C.c_double), ("sigma", C.c_double), ("chi2_dof", C.c_double), ("n_points", C.c_int64),
                 ("order", C.c_int32), ("sector", C.c_int32), ("n_nonfinite", C.c_int64), ("precision", C.c_int32),
-                ("unit", C.c_int32), ("fp32_error", C.c_double)]
+                ("unit", C.c_int32), ("part", C.c_int32), ("pad", C.c_int32), ("fp32_error", C.c_double)]
 
 
 class Stats(C.Structure):

@@ -25,6 +25,26 @@ class Result:
     assembled_errors: dict = None
 
 
+def _n_orders(u):
+    return u.n_out // 2 if u.cplx else u.n_out
+
+
+def _record_key(u, o):
+    """(eps order, part) of result o of unit u; part 1 is an imaginary part."""
+    return (u.order + o // 2, o & 1) if u.cplx else (u.order + o, 0)
+
+
+def _sum_parts(records):
+    """Sums over units per eps order of (order, part, value, sigma) records: complex
+    values, and errors complex(sigma_re, sigma_im) each combined in the mean-square norm."""
+    v, e = {}, {}
+    for K, part, val, sig in records:
+        v.setdefault(K, [0.0, 0.0])[part] += val
+        e.setdefault(K, [0.0, 0.0])[part] += sig * sig
+    return ({K: complex(*x) for K, x in v.items()},
+            {K: complex(math.sqrt(x[0]), math.sqrt(x[1])) for K, x in e.items()})
+
+
 class Integrator:
     """Holds the device copy of a Prepared set of units (one fiesta_ctx)."""
 
@@ -52,7 +72,7 @@ class Integrator:
                                  u.order, u.sector, u.rng_key & 0xFFFFFFFF,
                                  code.ctypes.data_as(C.POINTER(C.c_uint32)),
                                  cons.ctypes.data_as(C.POINTER(C.c_double)), int(u.n_out),
-                                 outs.ctypes.data_as(C.POINTER(C.c_int32)))
+                                 outs.ctypes.data_as(C.POINTER(C.c_int32)), int(bool(u.cplx)))
         self._keep = keep
         alloc = None
         if torch_alloc:
@@ -80,7 +100,7 @@ class Integrator:
                   iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
                   probe_points=0, fp32_budget=0.0, graph=True):
         lo = min(u.order for u in self.prep.units)
-        hi = max(u.order + u.n_out - 1 for u in self.prep.units)
+        hi = max(u.order + _n_orders(u) - 1 for u in self.prep.units)
         nord = hi - lo + 1
         b, e = (0, len(self.prep.units)) if units is None else units
         opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(adapt), int(points),
@@ -95,11 +115,14 @@ class Integrator:
             rc = self.lib.fiesta_integrate(self.ctx, C.byref(opt), val, err, nord, per, C.byref(st))
         if rc != N.FIESTA_OK and not (rc == -5 and not raise_nonfinite):
             N.check(rc)
-        values = {lo + k: val[k] for k in range(nord)}
-        errors = {lo + k: err[k] for k in range(nord)}
         pu = [dict(value=r.value, sigma=r.sigma, chi2_dof=r.chi2_dof, n_points=r.n_points, order=r.order,
                    sector=r.sector, n_nonfinite=r.n_nonfinite, precision=("fp64", "fp32")[r.precision],
-                   unit=r.unit, fp32_error=r.fp32_error) for r in per]
+                   unit=r.unit, fp32_error=r.fp32_error, part=r.part) for r in per]
+        if self.prep.complex:
+            values, errors = _sum_parts([(d["order"], d["part"], d["value"], d["sigma"]) for d in pu])
+        else:
+            values = {lo + k: val[k] for k in range(nord)}
+            errors = {lo + k: err[k] for k in range(nord)}
         stats = dict(gpu_ms=st.gpu_ms, eval_ms=st.eval_ms, points=st.points, points_per_s=st.points_per_s,
                      kernels_launched=st.kernels_launched, eval_launches=st.eval_launches,
                      units_fp32=st.units_fp32, unit_points=st.unit_points, threads=tuple(st.threads),
@@ -112,9 +135,11 @@ class Integrator:
     # ------------------------------------------------------------------ per point
     def eval_batch(self, unit, x, precision="fp64"):
         """f at points x (n, dim): a torch CUDA tensor (result on the device) or a host array.
-        A fused unit returns (n, n_out)."""
+        A fused unit returns (n, n_out); a complex unit returns complex values, (n,) for
+        one order or (n, n_out / 2) for several."""
         torch = self._torch
-        nout = self.prep.units[unit].n_out
+        u = self.prep.units[unit]
+        nout = u.n_out
         shape = (x.shape[0],) if nout == 1 else (x.shape[0], nout)
         if isinstance(x, torch.Tensor) and x.is_cuda:
             x = x.to(torch.float64).contiguous()
@@ -122,12 +147,18 @@ class Integrator:
             with torch.cuda.device(self.device):
                 N.check(self.lib.fiesta_eval_batch(self.ctx, int(unit), N.PRECISION[precision],
                                                    C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(f.data_ptr())))
+            if u.cplx:
+                f = torch.view_as_complex(f.view(x.shape[0], nout // 2, 2))
+                return f[:, 0] if nout == 2 else f
             return f
         x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
         f = np.empty(shape)
         with torch.cuda.device(self.device):
             N.check(self.lib.fiesta_eval_batch(self.ctx, int(unit), N.PRECISION[precision],
                                                x.ctypes.data_as(C.c_void_p), x.shape[0], f.ctypes.data_as(C.c_void_p)))
+        if u.cplx:
+            f = f[:, 0::2] + 1j * f[:, 1::2]
+            return f[:, 0] if nout == 2 else f
         return f
 
     def precision_probe(self, n_points=16384, seed=1, units=None):
@@ -344,15 +375,19 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
             continue
         val = swi / sw
         sig = np.sqrt(1.0 / sw)
-        values, errors = {}, {}
-        for k, (unit, o) in enumerate(recs):
-            K = prep.units[unit].order + o
-            values[K] = values.get(K, 0.0) + val[k]
-            errors[K] = errors.get(K, 0.0) + sig[k] ** 2
-        errors = {K: math.sqrt(e) for K, e in errors.items()}
+        if prep.complex:
+            values, errors = _sum_parts([_record_key(prep.units[unit], o) + (val[k], sig[k])
+                                         for k, (unit, o) in enumerate(recs)])
+        else:
+            values, errors = {}, {}
+            for k, (unit, o) in enumerate(recs):
+                K = prep.units[unit].order + o
+                values[K] = values.get(K, 0.0) + val[k]
+                errors[K] = errors.get(K, 0.0) + sig[k] ** 2
+            errors = {K: math.sqrt(e) for K, e in errors.items()}
         R, E = assemble(prep, values, errors)
         big = max(abs(v) for v in R.values())
-        ok = all(E[n] <= target * max(abs(R[n]), floor * big) for n in R)
+        ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)
         res = dict(gpu_s=gpu_ms * 1e-3, points=points_done, iterations=it, values=R, errors=E, converged=ok,
                    unit_values=val.copy(), unit_sigmas=sig.copy())
         if ok or (stop_after is not None and it >= stop_after):
@@ -399,7 +434,7 @@ def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, st
         errors = {K: math.sqrt(e) for K, e in errors.items()}
         R, E = assemble(prep, values, errors)
         big = max(abs(x) for x in R.values())
-        ok = all(E[n] <= target * max(abs(R[n]), floor * big) for n in R)
+        ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)
         res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=r + 1, values=R, errors=E, converged=ok,
                    unit_values=val.copy(), unit_sigmas=sig.copy())
         if ok and r >= train_rounds:

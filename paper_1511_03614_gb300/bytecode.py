@@ -23,6 +23,7 @@ Opcodes (slot[i] is written s[i], c[k] a constant, x[j] a coordinate):
 13    LOG    s[d] = log(s[a])
 14    INV    s[d] = 1 / s[a]
 15    MOV    s[d] = s[a]
+16    ATAN2  s[d] = atan2(s[a], s[b])  (argument of a complex value)
 ====  =====  =========================================
 
 An instruction reads its operands before it writes s[d], so d may equal a or b.
@@ -35,7 +36,7 @@ import dataclasses
 import numpy as np
 
 OPS = {"LDX": 1, "LDC": 2, "ADD": 3, "SUB": 4, "MUL": 5, "DIV": 6, "NEG": 7, "MAC": 8,
-       "ADDC": 9, "MULC": 10, "MACC": 11, "POWI": 12, "LOG": 13, "INV": 14, "MOV": 15}
+       "ADDC": 9, "MULC": 10, "MACC": 11, "POWI": 12, "LOG": 13, "INV": 14, "MOV": 15, "ATAN2": 16}
 NAMES = {v: k for k, v in OPS.items()}
 MAX_SLOTS = 255
 MAX_CONST = 65536
@@ -72,7 +73,7 @@ class Program:
 
 
 def _args(n):
-    if n[0] in ("add", "sub", "mul", "div"):
+    if n[0] in ("add", "sub", "mul", "div", "atan2"):
         return (n[1], n[2])
     if n[0] == "fma":
         return (n[1], n[2], n[3])
@@ -163,7 +164,7 @@ def emit(graph, out, dim):
             continue
         live.add(i)
         n = nodes[i]
-        if n[0] in ("add", "sub", "mul", "div"):
+        if n[0] in ("add", "sub", "mul", "div", "atan2"):
             stack += [n[1], n[2]]
         elif n[0] == "fma":
             stack += [n[1], n[2], n[3]]
@@ -200,7 +201,7 @@ def emit(graph, out, dim):
     for pos, i in enumerate(order):
         n = nodes[i]
         args = ()
-        if n[0] in ("add", "sub", "mul", "div"):
+        if n[0] in ("add", "sub", "mul", "div", "atan2"):
             args = (n[1], n[2])
         elif n[0] == "fma":
             args = (n[1], n[2], n[3])
@@ -240,7 +241,7 @@ def emit(graph, out, dim):
             continue                      # only used folded
         # release operands whose last use is here (their slots may be reused by dst)
         args = ()
-        if kind in ("add", "sub", "mul", "div"):
+        if kind in ("add", "sub", "mul", "div", "atan2"):
             args = (n[1], n[2])
         elif kind == "fma":
             args = (n[1], n[2], n[3])
@@ -282,7 +283,7 @@ def emit(graph, out, dim):
                 put("ADDC" if kind == "add" else "MULC", d, slot[other], const_index(nodes[cnode][1]))
             else:
                 put(kind.upper(), d, slot[n[1]], slot[n[2]])
-        elif kind in ("sub", "div"):
+        elif kind in ("sub", "div", "atan2"):
             put(kind.upper(), d, slot[n[1]], slot[n[2]])
         elif kind in ("neg", "log", "inv"):
             put(kind.upper(), d, slot[n[1]])
@@ -323,7 +324,7 @@ def validate(prog):
         elif name == "LDC":
             if (a | b << 8) >= nc:
                 raise ValueError(f"constant out of range at {pc}")
-        elif name in ("ADD", "SUB", "MUL", "DIV"):
+        elif name in ("ADD", "SUB", "MUL", "DIV", "ATAN2"):
             reads = [a, b]
         elif name == "MAC":
             reads = [a, b, d]

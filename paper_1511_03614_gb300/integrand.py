@@ -231,3 +231,276 @@ def sector_graph(sec, orders):
         node = ev.unit(K) if K >= -len(ev.S) else None
         outs.append(g.c(0.0) if node is None else node)
     return g, outs
+
+
+# ---------------------------------------------------------------------------
+# Physical kinematics: contour deformation
+# ---------------------------------------------------------------------------
+
+from .ir import cconst, cadd, csub, cmul, cscale, cinv, cpowi, clog  # noqa: E402
+from .poly import pderiv  # noqa: E402
+
+
+class _ComplexSectorEval:
+    """The sector integrand on a deformed contour.
+
+    With F the sector's last polynomial (the second Symanzik polynomial after the
+    monomial factor is pulled out), the variables move to
+    z_j = t_j - i lam t_j (1 - t_j) dF/dt_j.  The deformation vanishes on the faces
+    t_j = 0, 1, so the integral over the cube is unchanged, and Im F(z) <= 0 for small
+    lam realises the F - i0 prescription of the propagators.  Writing
+    z_j = t_j w_j, the integrand prod z_j^{c_j + b_j eps} G(z) det(dz/dt) is
+    prod t_j^{c_j + b_j eps} times G~ = prod w_j^{c_j + b_j eps} G(z) det(dz/dt),
+    and G~ takes the place of G in the subtraction and expansion of ``_SectorEval``.
+    All quantities are (re, im) pairs of real graph nodes.
+    """
+
+    def __init__(self, g, sec, lam):
+        self.g = g
+        self.sec = sec
+        self.lam = float(lam)
+        self.pos = {j: i for i, j in enumerate(sec.variables)}
+        self.S = singular(sec)
+        F = sec.polys[-1][0]
+        self.D1 = {j: pderiv(F, j - 1) for j in sec.variables}
+        self.D2 = {(j, k): pderiv(self.D1[j], k - 1) for j in sec.variables for k in sec.variables}
+        self._c = {}
+
+    def t(self, j):
+        return self.g.x(self.pos[j])
+
+    def _tpow(self, j, e):
+        key = ("tp", j, e)
+        if key not in self._c:
+            g = self.g
+            if e == 1:
+                self._c[key] = self.t(j)
+            elif e % 2 == 0:
+                h = self._tpow(j, e // 2)
+                self._c[key] = g.mul(h, h)
+            else:
+                self._c[key] = g.mul(self._tpow(j, e - 1), self.t(j))
+        return self._c[key]
+
+    def rpoly(self, p, W):
+        """Real polynomial p at t with t_W = 0."""
+        g = self.g
+        acc = g.c(0.0)
+        for m, c in sorted(p.items()):
+            if any(m[j - 1] for j in W):
+                continue
+            mono = g.c(1.0)
+            for q, e in enumerate(m):
+                if e:
+                    mono = g.mul(mono, self._tpow(q + 1, e))
+            acc = g.fma(mono, g.c(float(c)), acc)
+        return acc
+
+    def w(self, j, W):
+        key = ("w", j, W)
+        if key not in self._c:
+            g = self.g
+            one_minus_t = g.c(1.0) if j in W else g.sub(g.c(1.0), self.t(j))
+            im = g.mul(g.mul(one_minus_t, self.rpoly(self.D1[j], W)), g.c(-self.lam))
+            self._c[key] = (g.c(1.0), im)
+        return self._c[key]
+
+    def zpow(self, j, e, W):
+        """z_j^e at the corner W (z_j = 0 for j in W)."""
+        key = ("zp", j, e, W)
+        if key not in self._c:
+            g = self.g
+            if j in W:
+                self._c[key] = cconst(g, 0.0)
+            elif e == 1:
+                wj = self.w(j, W)
+                self._c[key] = (self.t(j), g.mul(self.t(j), wj[1]))
+            elif e % 2 == 0:
+                h = self.zpow(j, e // 2, W)
+                self._c[key] = cmul(g, h, h)
+            else:
+                self._c[key] = cmul(g, self.zpow(j, e - 1, W), self.zpow(j, 1, W))
+        return self._c[key]
+
+    def cpoly(self, i, W):
+        key = ("P", i, W)
+        if key not in self._c:
+            g = self.g
+            acc = cconst(g, 0.0)
+            for m, c in sorted(self.sec.polys[i][0].items()):
+                if any(m[j - 1] for j in W):
+                    continue
+                mono = cconst(g, 1.0)
+                for q, e in enumerate(m):
+                    if e:
+                        mono = cmul(g, mono, self.zpow(q + 1, e, W))
+                acc = cadd(g, acc, cscale(g, mono, g.c(float(c))))
+            self._c[key] = acc
+        return self._c[key]
+
+    def detJ(self, W):
+        """det(dz/dt) = det(I - i lam M), M_jk = delta_jk (1 - 2 t_j) D_j + t_j (1 - t_j) D_jk,
+        by Gaussian elimination without pivoting (the matrix is close to the identity)."""
+        key = ("J", W)
+        if key in self._c:
+            return self._c[key]
+        g = self.g
+        V = list(self.sec.variables)
+        d = len(V)
+        A = [[None] * d for _ in range(d)]
+        for a, j in enumerate(V):
+            tj = g.c(0.0) if j in W else self.t(j)
+            tt = g.mul(tj, g.sub(g.c(1.0), tj))
+            for b, k in enumerate(V):
+                m = g.mul(tt, self.rpoly(self.D2[(j, k)], W))
+                if a == b:
+                    m = g.fma(g.sub(g.c(1.0), g.mul(tj, g.c(2.0))), self.rpoly(self.D1[j], W), m)
+                A[a][b] = (g.c(1.0 if a == b else 0.0), g.mul(m, g.c(-self.lam)))
+        det = cconst(g, 1.0)
+        for k in range(d):
+            piv = A[k][k]
+            det = cmul(g, det, piv)
+            if k + 1 == d:
+                break
+            ip = cinv(g, piv)
+            for i in range(k + 1, d):
+                f = cmul(g, A[i][k], ip)
+                for jj in range(k + 1, d):
+                    A[i][jj] = csub(g, A[i][jj], cmul(g, f, A[k][jj]))
+        self._c[key] = det
+        return det
+
+    def G_at(self, N, W):
+        key = ("G", N, W)
+        if key in self._c:
+            return self._c[key]
+        g = self.g
+        sec = self.sec
+        if N == 0:
+            out = self.detJ(W)
+            for j in sec.variables:
+                c = sec.mono[j][0]
+                if c:
+                    out = cmul(g, out, cpowi(g, self.w(j, W), c))
+            for i, (p, (a0, a1)) in enumerate(sec.polys):
+                if a0:
+                    out = cmul(g, out, cpowi(g, self.cpoly(i, W), a0))
+            for i, power in sec.log_factor:
+                out = cmul(g, out, cpowi(g, clog(g, self.cpoly(i, W)), power))
+        else:
+            L = cconst(g, 0.0)
+            for i, (p, (a0, a1)) in enumerate(sec.polys):
+                if a1:
+                    L = cadd(g, L, cscale(g, clog(g, self.cpoly(i, W)), g.c(float(a1))))
+            for j in sec.variables:
+                b = sec.mono[j][1]
+                if b:
+                    L = cadd(g, L, cscale(g, clog(g, self.w(j, W)), g.c(float(b))))
+            out = cscale(g, cmul(g, self.G_at(N - 1, W), L), g.c(1.0 / N))
+        self._c[key] = out
+        return out
+
+    def D(self, T, N):
+        key = ("D", T, N)
+        if key in self._c:
+            return self._c[key]
+        rest = [j for j in self.S if j not in T]
+
+        def diff(k, W):
+            if k == len(rest):
+                return self.G_at(N, tuple(sorted(W)))
+            j = rest[k]
+            return csub(self.g, diff(k + 1, W), diff(k + 1, W + (j,)))
+        out = diff(0, tuple(T))
+        self._c[key] = out
+        return out
+
+    def logt(self, j):
+        key = ("lt", j)
+        if key not in self._c:
+            self._c[key] = self.g.log(self.t(j))
+        return self._c[key]
+
+    def unit(self, K):
+        g = self.g
+        sec = self.sec
+        S = self.S
+        total = cconst(g, 0.0)
+        for T in _subsets(S):
+            top = K + len(T)
+            if top < 0:
+                continue
+            lam = g.c(0.0)
+            for j in sec.variables:
+                b = sec.mono[j][1]
+                if j not in T and b:
+                    lam = g.fma(self.logt(j), g.c(float(b)), lam)
+            inner = cconst(g, 0.0)
+            lam_pow = g.c(1.0)
+            for m in range(0, top + 1):
+                if m:
+                    if g.const_value(lam) == 0.0:
+                        break
+                    lam_pow = g.mul(g.mul(lam_pow, lam), g.c(1.0 / m))
+                Dn = self.D(T, top - m)
+                inner = cadd(g, inner, cscale(g, Dn, lam_pow))
+            fac = 1.0
+            for j in T:
+                fac /= sec.mono[j][1]
+            term = cscale(g, inner, g.c(fac))
+            for j in S:
+                if j not in T:
+                    term = cscale(g, term, g.inv(self.t(j)))
+            total = cadd(g, total, term)
+        mono = g.c(float(sec.coef))
+        for j in sec.variables:
+            if j in S:
+                continue
+            c = sec.mono[j][0]
+            if c:
+                mono = g.mul(mono, g.powi(self.t(j), c))
+        return cscale(g, total, mono)
+
+
+def sector_graph_complex(sec, orders, lam):
+    """(Graph, [re_K0, im_K0, re_K1, im_K1, ...]) of a sector on the deformed contour."""
+    g = Graph()
+    ev = _ComplexSectorEval(g, sec, lam)
+    outs = []
+    for K in orders:
+        if K < -len(ev.S):
+            outs += [g.c(0.0), g.c(0.0)]
+        else:
+            re, im = ev.unit(K)
+            outs += [re, im]
+    return g, outs
+
+
+def choose_lambda(sec, lam_max=1.0, n_points=2000, seed=0):
+    """Largest lam in lam_max * 2^-k (k = 0..12) with Im F(z) <= 0 and Re w_j > 0 at
+    random points of the cube, or None when F has only positive coefficients (no
+    deformation needed)."""
+    import numpy as np
+    F = sec.polys[-1][0]
+    if all(c > 0 for c in F.values()):
+        return None
+    rng = np.random.default_rng(seed)
+    var = sec.variables
+    X = rng.uniform(1e-6, 1 - 1e-6, size=(n_points, len(var)))
+
+    def ev_poly(p, Z):
+        out = np.zeros(Z.shape[0], dtype=Z.dtype)
+        for m, c in p.items():
+            term = np.full(Z.shape[0], float(c), dtype=Z.dtype)
+            for q, e in enumerate(m):
+                if e:
+                    term = term * Z[:, var.index(q + 1)] ** e
+            out = out + term
+        return out
+    D = np.stack([ev_poly(pderiv(F, j - 1), X) for j in var], axis=1)
+    for k in range(13):
+        lam = lam_max * 2.0 ** -k
+        Z = X - 1j * lam * X * (1 - X) * D
+        if np.all(np.imag(ev_poly(F, Z)) <= 0.0):
+            return lam
+    raise ValueError("no contour deformation parameter keeps Im F <= 0")

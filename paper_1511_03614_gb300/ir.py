@@ -140,6 +140,12 @@ class Graph:
             return self.c(math.log(ca))
         return self._add(("log", a))
 
+    def atan2(self, y, x):
+        cy, cx = self.const_value(y), self.const_value(x)
+        if cy is not None and cx is not None:
+            return self.c(math.atan2(cy, cx))
+        return self._add(("atan2", y, x))
+
     def sum(self, items):
         out = self.c(0.0)
         for i in items:
@@ -151,3 +157,72 @@ class Graph:
         for i in items:
             out = self.mul(out, i)
         return out
+
+
+# ---------------------------------------------------------------------------
+# Complex values as pairs (re, im) of real nodes.  A constant zero imaginary part
+# folds away, so purely real computations cost nothing extra.
+# ---------------------------------------------------------------------------
+
+def cconst(g, re, im=0.0):
+    return (g.c(re), g.c(im))
+
+
+def creal(g, x):
+    return (x, g.c(0.0))
+
+
+def cadd(g, x, y):
+    return (g.add(x[0], y[0]), g.add(x[1], y[1]))
+
+
+def csub(g, x, y):
+    return (g.sub(x[0], y[0]), g.sub(x[1], y[1]))
+
+
+def cmul(g, x, y):
+    return (g.sub(g.mul(x[0], y[0]), g.mul(x[1], y[1])), g.fma(x[0], y[1], g.mul(x[1], y[0])))
+
+
+def cscale(g, x, r):
+    """complex x times real node r"""
+    return (g.mul(x[0], r), g.mul(x[1], r))
+
+
+def cfma(g, x, y, acc):
+    """x * y + acc"""
+    re = g.sub(g.fma(x[0], y[0], acc[0]), g.mul(x[1], y[1]))
+    im = g.fma(x[0], y[1], g.fma(x[1], y[0], acc[1]))
+    return (re, im)
+
+
+def cinv(g, x):
+    if g.const_value(x[1]) == 0.0:
+        return (g.inv(x[0]), g.c(0.0))
+    d = g.fma(x[0], x[0], g.mul(x[1], x[1]))
+    r = g.inv(d)
+    return (g.mul(x[0], r), g.neg(g.mul(x[1], r)))
+
+
+def cpowi(g, x, n):
+    if g.const_value(x[1]) == 0.0:
+        return (g.powi(x[0], n), g.c(0.0))
+    if n == 0:
+        return cconst(g, 1.0)
+    m = abs(n)
+    out, base = None, x
+    while m:
+        if m & 1:
+            out = base if out is None else cmul(g, out, base)
+        m >>= 1
+        if m:
+            base = cmul(g, base, base)
+    return cinv(g, out) if n < 0 else out
+
+
+def clog(g, x):
+    """Principal logarithm; a value with a constant zero imaginary part is taken as positive."""
+    if g.const_value(x[1]) == 0.0:
+        return (g.log(x[0]), g.c(0.0))
+    m2 = g.fma(x[0], x[0], g.mul(x[1], x[1]))
+    return (g.mul(g.log(m2), g.c(0.5)), g.atan2(x[1], x[0]))

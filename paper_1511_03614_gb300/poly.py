@@ -97,3 +97,15 @@ def adjugate(mat):
             c = det(minor)
             adj[j][i] = c if (i + j) % 2 == 0 else pscale(c, -1)
     return adj
+
+
+def pderiv(p, i):
+    """Derivative with respect to exponent position i."""
+    out = {}
+    for m, c in p.items():
+        if m[i]:
+            mm = list(m)
+            mm[i] -= 1
+            mm = tuple(mm)
+            out[mm] = out.get(mm, 0) + c * m[i]
+    return {m: c for m, c in out.items() if c}

@@ -26,6 +26,8 @@ class Unit:
     program: B.Program
     rng_key: int
     n_out: int = 1            # results: orders order .. order + n_out - 1 (fused multi-order unit)
+    cplx: bool = False        # deformed contour: results are (re, im) pairs, orders order .. order + n_out/2 - 1
+    lam: float = None         # the deformation parameter of a complex unit
 
 
 @dataclasses.dataclass
@@ -36,48 +38,71 @@ class Prepared:
     int_orders: tuple         # eps orders of the parametric integral
     out_orders: tuple         # eps orders of the assembled result
     sectors: list
+    lams: list = None         # per sector: contour-deformation parameter, None when F > 0
+
+    @property
+    def complex(self):
+        return any(u.cplx for u in self.units)
 
     def flops_per_point(self):
         """Mean arithmetic operations per point over the units (see Program.flops)."""
         return sum(u.program.flops() for u in self.units) / max(len(self.units), 1)
 
 
-def _units_for(sectors, orders_of):
+def _real_units(si, sec, Ks, fuse):
+    """Units of a sector with F > 0: one per order, or one fused unit for all orders."""
+    if fuse:
+        if len(Ks) > MAX_OUT:
+            raise ValueError(f"a fused unit holds at most {MAX_OUT} orders")
+        g, outs = I.sector_graph(sec, Ks)
+        return [Unit(si, Ks[0], len(sec.variables), B.emit(g, outs, len(sec.variables)), 0,
+                     n_out=len(Ks))]
     units = []
-    for si, sec in enumerate(sectors):
-        for K in orders_of(sec):
-            r = I.unit_graph(sec, K)
-            if r is None:
-                continue
-            g, out = r
-            prog = B.emit(g, out, len(sec.variables))
-            units.append(Unit(si, K, len(sec.variables), prog, len(units)))
+    for K in Ks:
+        r = I.unit_graph(sec, K)
+        if r is None:
+            continue
+        g, out = r
+        units.append(Unit(si, K, len(sec.variables), B.emit(g, out, len(sec.variables)), 0))
+    return units
+
+
+def _complex_units(si, sec, Ks, fuse, lam):
+    """Units of a sector on the deformed contour: each order gives a (re, im) pair of
+    results; fused while the pairs fit MAX_OUT results, else one unit per order."""
+    groups = [Ks] if fuse and 2 * len(Ks) <= MAX_OUT else [[K] for K in Ks]
+    units = []
+    for grp in groups:
+        g, outs = I.sector_graph_complex(sec, grp, lam)
+        units.append(Unit(si, grp[0], len(sec.variables), B.emit(g, outs, len(sec.variables)), 0,
+                          n_out=2 * len(grp), cplx=True, lam=lam))
     return units
 
 
 MAX_OUT = 6
 
 
-def _fused_units(sectors, orders_of):
-    """One unit per sector whose program returns every eps order of the sector: the
-    orders share the polynomial values, logarithms and corner terms (one evaluation
-    of U, F and the subtraction corners per point instead of one per order)."""
-    units = []
-    for si, sec in enumerate(sectors):
-        Ks = list(orders_of(sec))
-        if not Ks:
-            continue
-        if len(Ks) > MAX_OUT:
-            raise ValueError(f"a fused unit holds at most {MAX_OUT} orders")
-        g, outs = I.sector_graph(sec, Ks)
-        prog = B.emit(g, outs, len(sec.variables))
-        units.append(Unit(si, Ks[0], len(sec.variables), prog, len(units), n_out=len(Ks)))
-    return units
+def _sector_lambda(sec, lam, lam_max):
+    """None when every coefficient of F is positive (no deformation needed)."""
+    if all(c > 0 for c in sec.polys[-1][0].values()):
+        return None
+    if callable(lam):
+        return lam(sec)
+    if lam is not None:
+        return float(lam)
+    return I.choose_lambda(sec, lam_max)
 
 
-def prepare_feynman(problem, strategy="M", fuse_orders=False):
+def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=1.0):
     """Units of a Feynman integral; with ``fuse_orders`` one unit per sector carries all
-    its eps orders (a vector-valued integrand with one Vegas grid)."""
+    its eps orders (a vector-valued integrand with one Vegas grid).
+
+    Sectors whose F has a coefficient that is not positive (physical kinematics) are
+    integrated on a deformed contour (``integrand.sector_graph_complex``) with complex
+    results; ``lam`` fixes the deformation parameter (a number, or a callable of the
+    sector), else it is chosen per sector by ``integrand.choose_lambda`` up to lam_max.
+    A sector where no parameter keeps Im F <= 0 raises ValueError.
+    """
     U, F = symanzik(problem)
     n = len(problem.propagators)
     L = len(problem.loop_momenta)
@@ -85,11 +110,22 @@ def prepare_feynman(problem, strategy="M", fuse_orders=False):
     kmin = min(I.min_order(s) for s in secs)
     q0, _ = PF.series(problem.indices, L, 0)
     khi = problem.order + q0
-    orders_of = lambda s: range(max(kmin, I.min_order(s)), khi + 1)
-    units = (_fused_units if fuse_orders else _units_for)(secs, orders_of)
+    units, lams = [], []
+    for si, sec in enumerate(secs):
+        Ks = list(range(max(kmin, I.min_order(sec)), khi + 1))
+        lm = _sector_lambda(sec, lam, lam_max)
+        lams.append(lm)
+        if not Ks:
+            continue
+        if lm is None:
+            units += _real_units(si, sec, Ks, fuse_orders)
+        else:
+            units += _complex_units(si, sec, Ks, fuse_orders, lm)
+    for k, u in enumerate(units):
+        u.rng_key = k
     pre = PF.series(problem.indices, L, problem.order - kmin)
     return Prepared(problem.name, units, pre, tuple(range(kmin, khi + 1)),
-                    tuple(range(kmin - pre[0], problem.order + 1)), secs)
+                    tuple(range(kmin - pre[0], problem.order + 1)), secs, lams)
 
 
 def prepare_direct(problems, name="direct"):
@@ -123,10 +159,19 @@ def assemble(prep, values, errors, correlated=None):
     sector at the same points, so I_K of different K are correlated; then the
     bound sigma_n <= sum_m |c_m| sigma_{n-m}, valid for any correlation, is used.
     ``values``/``errors`` map eps orders of the parametric integral to sums over
-    sectors (errors combined in the mean-square norm, Sec. 4.3).
+    sectors (errors combined in the mean-square norm, Sec. 4.3).  Complex values
+    (deformed contour) come with errors complex(sigma_re, sigma_im); the prefactor
+    series is real, so the real and imaginary parts are assembled separately.
     """
+    if any(isinstance(v, complex) for v in values.values()):
+        part = lambda d, f: {K: f(x) for K, x in d.items()}
+        Rr, Er = assemble(prep, part(values, lambda z: complex(z).real), part(errors, lambda z: complex(z).real),
+                          correlated)
+        Ri, Ei = assemble(prep, part(values, lambda z: complex(z).imag), part(errors, lambda z: complex(z).imag),
+                          correlated)
+        return ({n: complex(Rr[n], Ri[n]) for n in Rr}, {n: complex(Er[n], Ei[n]) for n in Er})
     if correlated is None:
-        correlated = any(getattr(u, "n_out", 1) > 1 for u in prep.units)
+        correlated = any((u.n_out // 2 if u.cplx else u.n_out) > 1 for u in prep.units)
     q, c = prep.prefactor
     R, E = {}, {}
     for n in prep.out_orders:

@@ -48,6 +48,8 @@ def run(prog, X, dtype=np.float64):
                 s[d] = 1.0 / s[a]
             elif name == "MOV":
                 s[d] = s[a]
+            elif name == "ATAN2":
+                s[d] = np.arctan2(s[a], s[b])
     if len(prog.out_slots) > 1:
         return np.stack([s[o].copy() for o in prog.out_slots], axis=1)
     return s[prog.out_slot].copy()

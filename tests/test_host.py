@@ -144,3 +144,26 @@ def test_fused_programs_match_oracle(name):
                 assert np.all(Fv[:, k] == 0)
                 continue
             assert np.all(np.abs(Fv[:, k] - o.f_numpy(X)) <= 1e-13 * P.magnitude_numpy(o, X))
+
+
+@pytest.mark.parametrize("fuse", [False, True])
+def test_complex_programs_match_oracle(fuse):
+    """Physical box (s > 0, t < 0): each deformed-contour program returns, per eps
+    order, the real and imaginary parts of the oracle's deformed integrand."""
+    prob = W.box_physical()
+    prep = prepare_feynman(prob, fuse_orders=fuse)
+    assert prep.complex and all(u.cplx and u.n_out % 2 == 0 for u in prep.units)
+    lams = {l for l in prep.lams if l is not None}
+    assert len(lams) == 1
+    orc = P.feynman_problem(prob, lam=lams.pop())
+    by = {(u.sector, u.order): u for u in orc.units}
+    rng = np.random.default_rng(6)
+    for u in prep.units:
+        X = rng.uniform(0.02, 0.98, size=(24, u.dim))
+        Fv = run(u.program, X)
+        for k in range(u.n_out // 2):
+            o = by[(u.sector, u.order + k)]
+            b = o.f_numpy(X)
+            a = Fv[:, 2 * k] + 1j * Fv[:, 2 * k + 1]
+            assert np.all(np.abs(a - b) <= 1e-12 * np.maximum(P.magnitude_numpy(o, X), np.abs(b))), (u.sector, k)
+
