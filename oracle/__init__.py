@@ -20,6 +20,8 @@ it restates:
 * ``sobol``     Sobol sequence from primitive polynomials (Bratley-Fox construction)
 * ``vegas``     Lepage's VEGAS adaptive Monte Carlo (the default integrator, Sec. 4.4)
 * ``quadrature`` tensor tanh-sinh rule for low-dimensional exact checks
+* ``cuhre``     deterministic adaptive cubature (Genz-Malik rule, passes of region
+                splitting): the Cuhre alternative among the integrators of Sec. 4.4
 * ``pipeline``  end-to-end: units, integration, error combination (Sec. 4.3) and
                 assembly with the prefactor.
 
