@@ -201,6 +201,83 @@ int fiesta_set_grid(fiesta_ctx *ctx, int64_t unit, const double *grid);
 int fiesta_refine(fiesta_ctx *ctx, int32_t dim, int64_t n, double alpha, double *grid, const double *hist);
 
 /*
+ * Deterministic adaptive cubature, the Cuhre alternative to Vegas among the
+ * integrators of Sec. 4.4 (CurrentIntegrator = cuhreCuba).  The paper does not
+ * describe it; the library uses the degree-7 rule of Genz and Malik (J. Comput.
+ * Appl. Math. 6 (1980) 295) with its embedded degree-5 rule, region error
+ * |I7 - I5| per result, and splits a region in halves across the coordinate
+ * with the largest fourth difference (summed over the unit's results; ties go
+ * to the wider side, then the lower coordinate).  Subdivision runs in passes
+ * over all live regions of all units of the slice at once: evaluate every live
+ * region; a unit whose summed error is <= tau for every result stops; in the
+ * other units a region whose error is <= tau * its volume (for every result) is
+ * frozen and the others are split.  tau_o = max(abs_tol, rel_tol * |estimate_o|),
+ * the modulus of the (re, im) pair for complex units.  Units of dimension 1 are
+ * integrated as 2-dimensional ones that ignore the second coordinate.
+ *
+ * rel_tol, abs_tol: tolerances (> 0 and >= 0).  max_passes: pass limit (0: 40).
+ * max_regions: limit on frozen + live regions of the call (0: 2^22); when the
+ * next pass would exceed it, the call stops with the current estimates.
+ * order_lo, unit_begin, unit_end: as in fiesta_options.  timeout_ms: checked
+ * between passes (0: none).  threads: block size of the evaluation kernel
+ * (0: 128; a multiple of 32, <= 256).
+ */
+typedef struct {
+    double rel_tol;
+    double abs_tol;
+    int32_t max_passes;
+    int32_t order_lo;
+    int64_t max_regions;
+    int64_t unit_begin;
+    int64_t unit_end;
+    int64_t timeout_ms;
+    int32_t threads;
+    int32_t reserved[3];
+} fiesta_cuhre_options;
+
+/* One record per result of a unit (n_out per unit, in unit order). */
+typedef struct {
+    double value;             /* estimate: sum over frozen and live regions of I7 */
+    double error;             /* sum of the regions' |I7 - I5| */
+    int64_t n_regions;        /* frozen + live regions of the unit at the end */
+    int64_t n_points;         /* integrand evaluations spent on the unit */
+    int32_t order;            /* eps order of the result */
+    int32_t sector;
+    int32_t unit;
+    int32_t part;             /* complex units: 0 real, 1 imaginary part */
+    int32_t converged;        /* the unit met its tolerances */
+    int32_t passes;           /* passes in which the unit had live regions */
+} fiesta_cuhre_result;
+
+/*
+ * Run the cubature on units [unit_begin, unit_end).  value/error (caller-owned
+ * host arrays of n_orders doubles) receive per eps order order_lo + k the sum
+ * over units of the estimates (real parts) and the sum of their error
+ * estimates (the regions' errors are bounds, so they add linearly).  per_result
+ * (nullable, host) receives one record per result of the slice's units; stats
+ * (nullable) the device time and evaluations.  Device buffers are allocated
+ * through the context's allocator and kept for later calls.
+ * Errors: FIESTA_E_INVALID (bad options or slice), FIESTA_E_NOMEM,
+ * FIESTA_E_CUDA, FIESTA_E_TIMEOUT and FIESTA_E_NONFINITE (results are still
+ * written).
+ */
+int fiesta_cuhre(fiesta_ctx *ctx, const fiesta_cuhre_options *opt, double *value, double *error,
+                 int32_t n_orders, fiesta_cuhre_result *per_result, fiesta_stats *stats);
+
+/*
+ * The regions of unit `unit` evaluated in the last pass of the last
+ * fiesta_cuhre call and not split since (a unit that converged in an earlier
+ * pass has none).  Up to `cap` regions are written to the host arrays center and
+ * half (cap * m doubles each, m = max(dim, 2): the region is the box
+ * prod [center_j - half_j, center_j + half_j]), value and error (cap * n_out:
+ * I7 and |I7 - I5| per result) and axis (cap: the coordinate it would be split
+ * across); *n receives the number of such regions.  Exposed so that each
+ * region's rule can be checked on its own.  Errors: FIESTA_E_INVALID.
+ */
+int fiesta_cuhre_regions(fiesta_ctx *ctx, int64_t unit, int64_t cap, double *center, double *half, double *value,
+                         double *error, int32_t *axis, int64_t *n);
+
+/*
  * Measurement support (no counterpart in the paper): measured throughput of
  * the arithmetic pipes on the current device, used to turn an integrand's
  * instruction mix into a lower bound on its evaluation time.  out (host, >= 7

@@ -54,6 +54,19 @@ class Stats(C.Structure):
                 ("points_per_thread", C.c_int32 * 2)]
 
 
+class CuhreOptions(C.Structure):
+    _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_passes", C.c_int32),
+                ("order_lo", C.c_int32), ("max_regions", C.c_int64), ("unit_begin", C.c_int64),
+                ("unit_end", C.c_int64), ("timeout_ms", C.c_int64), ("threads", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
+
+
+class CuhreResult(C.Structure):
+    _fields_ = [("value", C.c_double), ("error", C.c_double), ("n_regions", C.c_int64), ("n_points", C.c_int64),
+                ("order", C.c_int32), ("sector", C.c_int32), ("unit", C.c_int32), ("part", C.c_int32),
+                ("converged", C.c_int32), ("passes", C.c_int32)]
+
+
 EXPORTS = {
     "fiesta_load_sectors": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Program), C.c_int64, C.POINTER(Alloc),
                                       C.c_void_p]),
@@ -81,6 +94,11 @@ EXPORTS = {
                                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_float)]),
+    "fiesta_cuhre": (C.c_int, [C.c_void_p, C.POINTER(CuhreOptions), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.c_int32, C.POINTER(CuhreResult), C.POINTER(Stats)]),
+    "fiesta_cuhre_regions": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "fiesta_free": (None, [C.c_void_p]),
     "fiesta_last_error": (C.c_char_p, []),
     "fiesta_version": (C.c_int, []),

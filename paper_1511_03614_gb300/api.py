@@ -132,6 +132,64 @@ class Integrator:
             res.assembled, res.assembled_errors = assemble(self.prep, values, errors)
         return res
 
+    # ------------------------------------------------------------------ cubature
+    def cuhre(self, rel_tol=1e-6, abs_tol=1e-12, max_passes=40, max_regions=1 << 22, units=None, timeout_ms=0,
+              threads=0, assemble_result=True):
+        """Deterministic adaptive cubature (Genz-Malik rule, region splitting in passes)
+        of every unit: per-order values and errors (summed linearly: the region errors
+        are bounds), per-result records (value, error, regions, points, converged) and,
+        for the whole problem, the assembled series (linear error bound)."""
+        lo = min(u.order for u in self.prep.units)
+        hi = max(u.order + _n_orders(u) - 1 for u in self.prep.units)
+        nord = hi - lo + 1
+        b, e = (0, len(self.prep.units)) if units is None else units
+        opt = N.CuhreOptions(float(rel_tol), float(abs_tol), int(max_passes), lo, int(max_regions), int(b), int(e),
+                             int(timeout_ms), int(threads))
+        val = (C.c_double * nord)()
+        err = (C.c_double * nord)()
+        per = (N.CuhreResult * sum(u.n_out for u in self.prep.units[b:e]))()
+        st = N.Stats()
+        with self._torch.cuda.device(self.device):
+            N.check(self.lib.fiesta_cuhre(self.ctx, C.byref(opt), val, err, nord, per, C.byref(st)))
+        pu = [dict(value=r.value, error=r.error, n_regions=r.n_regions, n_points=r.n_points, order=r.order,
+                   sector=r.sector, unit=r.unit, part=r.part, converged=bool(r.converged), passes=r.passes)
+              for r in per]
+        if self.prep.complex:
+            values, errors = {}, {}
+            for d in pu:
+                values.setdefault(d["order"], [0.0, 0.0])[d["part"]] += d["value"]
+                errors.setdefault(d["order"], [0.0, 0.0])[d["part"]] += d["error"]
+            values = {K: complex(*x) for K, x in values.items()}
+            errors = {K: complex(*x) for K, x in errors.items()}
+        else:
+            values = {lo + k: val[k] for k in range(nord)}
+            errors = {lo + k: err[k] for k in range(nord)}
+        stats = dict(gpu_ms=st.gpu_ms, eval_ms=st.eval_ms, points=st.points, points_per_s=st.points_per_s,
+                     kernels_launched=st.kernels_launched, eval_launches=st.eval_launches,
+                     unit_points=st.unit_points)
+        res = Result(values, errors, pu, stats)
+        if assemble_result and units is None:
+            res.assembled, res.assembled_errors = assemble(self.prep, values, errors, correlated=True)
+        return res
+
+    def cuhre_regions(self, unit, cap=1 << 20):
+        """The regions of ``unit`` evaluated in the last pass of the last cuhre call:
+        (center (n, m), half (n, m), value (n, n_out), error (n, n_out), axis (n,)), m = max(dim, 2)."""
+        u = self.prep.units[unit]
+        m = max(u.dim, 2)
+        n = C.c_int64()
+        with self._torch.cuda.device(self.device):
+            N.check(self.lib.fiesta_cuhre_regions(self.ctx, int(unit), 0, None, None, None, None, None, C.byref(n)))
+        k = min(n.value, cap)
+        cen, half = np.zeros((k, m)), np.zeros((k, m))
+        val, err = np.zeros((k, u.n_out)), np.zeros((k, u.n_out))
+        ax = np.zeros(k, dtype=np.int32)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        with self._torch.cuda.device(self.device):
+            N.check(self.lib.fiesta_cuhre_regions(self.ctx, int(unit), k, dp(cen), dp(half), dp(val), dp(err),
+                                                  ax.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)))
+        return cen, half, val, err, ax
+
     # ------------------------------------------------------------------ per point
     def eval_batch(self, unit, x, precision="fp64"):
         """f at points x (n, dim): a torch CUDA tensor (result on the device) or a host array.
