@@ -31,6 +31,7 @@ WORKLOADS = {
     # name: (points per unit per iteration, iterations, rng)
     "box": (1_000_000, 10, "philox"),
     "bubble": (100_000, 10, "philox"),
+    "box_physical": (1_000_000, 10, "philox"),
     "double_box": (1_000_000, 1, "philox"),
     "stress": (1 << 20, 1, "sobol"),
 }
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fuse", type=int, default=1, help="1: one unit per sector carrying all its eps orders")
+    ap.add_argument("--forms", default="fp64,auto,fp32,flow_fp32,cuhre_fp64",
+                    help="tta mode: comma-separated forms to run")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "tta"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
     ap.add_argument("--target", type=float, default=1e-4)
@@ -156,16 +159,17 @@ def op_costs(peaks):
     fma_rate = peaks[0] * 1e12 / 2.0                 # binary64 FMA per second
     log_c = fma_rate / (peaks[6] * 1e9)
     div_c = fma_rate / (peaks[2] * 1e9)
-    return {"LOG": log_c, "DIV": div_c, "INV": div_c}
+    atan_c = fma_rate / (peaks[7] * 1e9) if len(peaks) > 7 and peaks[7] > 0 else log_c
+    return {"LOG": log_c, "DIV": div_c, "INV": div_c, "ATAN2": atan_c}
 
 
 def unit_work(prog, costs, dim, adapt):
     """(algorithmic flops, FMA-equivalent pipe slots) per point of one unit.
 
     Flops: ADD SUB MUL NEG ADDC MULC = 1, MAC MACC = 2, POWI = its multiplies,
-    DIV INV LOG = 1; plus the Vegas map (4 per coordinate: scale, edge difference,
+    DIV INV LOG ATAN2 = 1; plus the Vegas map (4 per coordinate: scale, edge difference,
     interpolation FMA, Jacobian product) and the accumulation (v = f J, v^2, two
-    sums: 4).  Pipe slots weigh LOG/DIV/INV by their measured cost.
+    sums: 4).  Pipe slots weigh LOG/DIV/INV/ATAN2 by their measured cost.
     """
     c = prog.counts
     flops = prog.flops()
@@ -176,9 +180,9 @@ def unit_work(prog, costs, dim, adapt):
             e = e - 256 if e >= 128 else e
             m = abs(e)
             powi += max(m.bit_length() - 1 + bin(m).count("1") - 1, 0) + (1 if e < 0 else 0)
-    flops += powi + c.get("DIV", 0) + c.get("INV", 0) + c.get("LOG", 0)
+    flops += powi + c.get("DIV", 0) + c.get("INV", 0) + c.get("LOG", 0) + c.get("ATAN2", 0)
     slots = prog.flops() / 1.0 - (c.get("MAC", 0) + c.get("MACC", 0)) + powi + \
-        sum(costs[k] * c.get(k, 0) for k in ("LOG", "DIV", "INV"))
+        sum(costs[k] * c.get(k, 0) for k in ("LOG", "DIV", "INV", "ATAN2"))
     extra = 4 * dim + 4
     return flops + extra, slots + extra
 
@@ -196,8 +200,8 @@ def run_ours(args):
     iters = args.iters or iters
     prep = prepared(args.workload, args.fuse)
     lib = N.load()
-    peaks = (C.c_double * 7)()
-    N.check(lib.fiesta_probe_peaks(peaks, 7))
+    peaks = (C.c_double * 8)()
+    N.check(lib.fiesta_probe_peaks(peaks, 8))
     peaks = list(peaks)
     integ = Integrator(prep)
     # replicas: every rank integrates every unit with its own point streams (weak scaling)
@@ -258,7 +262,7 @@ def run_ours(args):
                 "eval_ms_per_launch": avg_eval_s * 1e3,
                 "peaks_measured": {"fp64_tflops": peaks[0], "fp64_log_cuda_gps": peaks[1], "fp64_div_gps": peaks[2],
                                    "fp32_tflops": peaks[3], "fp32_log_gps": peaks[4], "fp32_div_gps": peaks[5],
-                                   "fp64_log_table_gps": peaks[6]},
+                                   "fp64_log_table_gps": peaks[6], "fp64_atan2_gps": peaks[7]},
                 "op_costs_fma_slots": costs}
 
     # end to end through the public API with host buffers: upload programs, integrate,
@@ -298,6 +302,9 @@ def run_ours(args):
             "config": {"workload": {"box": "one-loop massless box s=-1 t=-2, eps^-2..eps^0, 12 sectors x 3 dims "
                                            "(32 units), Vegas 10 it x 1e6 Philox points per unit",
                                     "bubble": "one-loop massless bubble p^2=-1 to eps^2, 8 units, 10 x 1e5",
+                                    "box_physical": "one-loop massless box at the physical point s=3 t=-1 (F changes "
+                                                    "sign): contour deformation, complex results, eps^-2..eps^0, "
+                                                    "12 sectors x 3 dims, Vegas 10 it x 1e6 Philox points per unit",
                                     "double_box": "planar double box s=t=-1, eps^-4..eps^0, 293 sectors x 6 dims",
                                     "stress": "10000 seeded synthetic integrands, dims 3..8, 2^20 Sobol points"
                                     }[args.workload],
@@ -314,13 +321,28 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": ck,
-            "results": {str(n): [res.assembled[n], res.assembled_errors[n]] for n in res.assembled}
+            "results": {str(n): [_num(res.assembled[n]), _num(res.assembled_errors[n])] for n in res.assembled}
             if res and res.assembled else None,
         }
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _oracle_lam(workload):
+    """Contour-deformation parameter for the oracle's physical-point workloads (the
+    value the preprocessor picks for every sector of the physical box)."""
+    return 1.0 if workload == "box_physical" else None
+
+
+def _real_f(unit):
+    """The oracle unit's integrand as a real function for the timing loop: a complex
+    unit is evaluated in full and its real part sampled."""
+    if getattr(unit, "complex", False):
+        import numpy as np
+        return lambda X: np.real(unit.f_numpy(X))
+    return unit.f_numpy
 
 
 def cpu_baseline(prep_unused, workload, budget_s):
@@ -332,14 +354,14 @@ def cpu_baseline(prep_unused, workload, budget_s):
         probs = W.stress_suite(200)
         units = [P.direct_problem(p).units[0] for p in probs]
     else:
-        units = P.feynman_problem(getattr(W, workload)()).units
+        units = P.feynman_problem(getattr(W, workload)(), lam=_oracle_lam(workload)).units
     n = 20000
     done = 0
     t0 = time.perf_counter()
     k = 0
     while time.perf_counter() - t0 < budget_s and k < 10 * len(units):
         u = units[k % len(units)]
-        V.integrate_unit(u.f_numpy, u.dim, 1, n, 1, k % len(units), rng="philox" if workload != "stress" else "sobol")
+        V.integrate_unit(_real_f(u), u.dim, 1, n, 1, k % len(units), rng="philox" if workload != "stress" else "sobol")
         done += n
         k += 1
     dt = time.perf_counter() - t0
@@ -357,16 +379,16 @@ def run_reference(args):
     if args.workload == "stress":
         units = [P.direct_problem(p).units[0] for p in W.stress_suite(100)]
     else:
-        units = P.feynman_problem(getattr(W, args.workload)()).units
+        units = P.feynman_problem(getattr(W, args.workload)(), lam=_oracle_lam(args.workload)).units
     n = 20000
     for _ in range(args.warmup):
-        V.integrate_unit(units[0].f_numpy, units[0].dim, 1, 2000, 1, 0, rng=rng)
+        V.integrate_unit(_real_f(units[0]), units[0].dim, 1, 2000, 1, 0, rng=rng)
     times = []
     done = 0
     for s in range(args.steps):
         t0 = time.perf_counter()
         for k, u in enumerate(units[:32]):
-            V.integrate_unit(u.f_numpy, u.dim, 1, n, 1 + s, k, rng=rng)
+            V.integrate_unit(_real_f(u), u.dim, 1, n, 1 + s, k, rng=rng)
             done += n
         times.append(time.perf_counter() - t0)
     total = sum(times)
@@ -382,6 +404,15 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+class _Skip(Exception):
+    """A tta form left out by --forms."""
+
+
+def _num(z):
+    """A JSON-able number: complex values as [re, im]."""
+    return [z.real, z.imag] if isinstance(z, complex) else z
+
+
 def run_tta(args):
     """GPU-seconds to the target relative error per eps order: plain binary64 Vegas
     against the per-unit mixed precision policy and binary32, same GPU, same points."""
@@ -394,7 +425,10 @@ def run_tta(args):
     out = {"mode": "tta", "workload": args.workload, "target": args.target, "points_per_unit_per_iter": pts,
            "units": len(prep.units), "runs": {}}
     from paper_1511_03614_gb300._native import FiestaError
+    forms = set(args.forms.split(","))
     for prec in ("fp64", "auto", "fp32"):
+        if prec not in forms:
+            continue
         integ = Integrator(prep)
         try:
             integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
@@ -405,19 +439,40 @@ def run_tta(args):
             continue
         out["runs"][prec] = {"gpu_s": r["gpu_s"], "points": r["points"], "iterations": r["iterations"],
                              "converged": r["converged"],
-                             "values": {str(n): [r["values"][n], r["errors"][n]] for n in r["values"]}}
+                             "values": {str(n): [_num(r["values"][n]), _num(r["errors"][n])] for n in r["values"]}}
         integ.close()
     # learned proposal: flow sampling with training rounds, binary32 integrand
     from paper_1511_03614_gb300.api import run_flow
     integ = Integrator(prep)
     try:
+        if "flow_fp32" not in forms:
+            raise _Skip()
         r = run_flow(integ, target=args.target, points=pts, keep=4096, train_rounds=8, steps_per_round=20,
                      max_rounds=300, precision="fp32")
         out["runs"]["flow_fp32"] = {"gpu_s": r["gpu_s"], "points": r["points"], "rounds": r["rounds"],
                                     "converged": r["converged"],
-                                    "values": {str(n): [r["values"][n], r["errors"][n]] for n in r["values"]}}
+                                    "values": {str(n): [_num(r["values"][n]), _num(r["errors"][n])] for n in r["values"]}}
     except FiestaError as e:
         out["runs"]["flow_fp32"] = {"error": str(e)}
+    except _Skip:
+        pass
+    integ.close()
+    # deterministic cubature (Genz-Malik rule, binary64), its error bound against the target
+    from paper_1511_03614_gb300.api import run_cuhre_to_accuracy
+    integ = Integrator(prepared(args.workload, fuse=True))
+    try:
+        if "cuhre_fp64" not in forms:
+            raise _Skip()
+        integ.cuhre(rel_tol=1e-2, max_passes=2)                                   # warm-up
+        r = run_cuhre_to_accuracy(integ, target=args.target)
+        out["runs"]["cuhre_fp64"] = {"gpu_s": r["gpu_s"], "points": r["points"], "rounds": r["rounds"],
+                                     "rel_tol": r["rel_tol"], "regions": r["regions"], "converged": r["converged"],
+                                     "values": {str(n): [_num(r["values"][n]), _num(r["errors"][n])]
+                                                for n in r["values"]}}
+    except FiestaError as e:
+        out["runs"]["cuhre_fp64"] = {"error": str(e)}
+    except _Skip:
+        pass
     integ.close()
     base = out["runs"].get("fp64", {}).get("gpu_s")
     out["speedup_vs_fp64"] = {k: base / v["gpu_s"] for k, v in out["runs"].items() if base and "gpu_s" in v}

@@ -127,7 +127,8 @@ typedef struct {
     int32_t kernels_launched; /* kernel launches made by this call */
     int32_t eval_launches;    /* of which evaluation-kernel launches */
     int64_t units_fp32;       /* units evaluated in binary32 */
-    int64_t unit_points;      /* points x results: evaluations of (sector, order) integrands */
+    int64_t unit_points;      /* evaluations of (sector, order) integrands: points x results, a
+                                 complex unit's (re, im) pair counting as one */
     int32_t threads[2];       /* block size used for binary64 [0] and binary32 [1] */
     int32_t points_per_thread[2];
 } fiesta_stats;
@@ -283,7 +284,8 @@ int fiesta_cuhre_regions(fiesta_ctx *ctx, int64_t unit, int64_t cap, double *cen
  * instruction mix into a lower bound on its evaluation time.  out (host, >= 7
  * doubles): [0] binary64 FMA TFLOP/s, [1] binary64 log (CUDA's) G/s, [2]
  * binary64 divide G/s, [3] binary32 FMA TFLOP/s, [4] binary32 logf G/s, [5]
- * binary32 divide G/s, [6] the interpreter's table-driven binary64 log G/s.
+ * binary32 divide G/s, [6] the interpreter's table-driven binary64 log G/s, and
+ * when n >= 8, [7] binary64 atan2 G/s.
  * Allocates and frees small scratch buffers.
  */
 int fiesta_probe_peaks(double *out, int32_t n);

@@ -453,6 +453,31 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
     return res
 
 
+def run_cuhre_to_accuracy(integ, target=1e-4, floor=1e-2, rel_tol=None, shrink=0.1, max_rounds=6, max_passes=60,
+                          max_regions=1 << 22):
+    """Adaptive cubature until every eps order of the assembled result has an error
+    bound <= target * max(|R|, floor * max|R|) (the rule of run_to_accuracy with the
+    cubature's linear error bound in place of sigma).  The per-unit relative
+    tolerance starts at ``rel_tol`` (default: target) and shrinks by ``shrink``
+    while the assembled bound misses the target (sector contributions can cancel);
+    GPU seconds add up over all attempts."""
+    tol = target if rel_tol is None else rel_tol
+    gpu_ms, pts, res = 0.0, 0, None
+    for k in range(max_rounds):
+        r = integ.cuhre(rel_tol=tol, max_passes=max_passes, max_regions=max_regions)
+        gpu_ms += r.stats["gpu_ms"]
+        pts += r.stats["points"]
+        R, E = r.assembled, r.assembled_errors
+        big = max(abs(v) for v in R.values())
+        ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)
+        res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=k + 1, rel_tol=tol, values=R, errors=E, converged=ok,
+                   regions=sum(d["n_regions"] for d in r.per_unit))
+        if ok:
+            break
+        tol *= shrink
+    return res
+
+
 def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, steps_per_round=20, lr=2e-3,
              power=1, max_rounds=200, seed=1, precision="fp32", floor=1e-2, skip_rounds=None):
     """Learned proposal: per unit, alternate flow sampling (an unbiased estimate each

@@ -780,7 +780,7 @@ int fiesta_cuhre(fiesta_ctx *c, const fiesta_cuhre_options *opt, double *value, 
     for (int64_t u = 0; u < nu; ++u) {
         const DevUnit &du = c->units[b + u];
         pts_all += npts[u];
-        unit_pts += npts[u] * NO[u];
+        unit_pts += npts[u] * (du.cplx ? NO[u] / 2 : NO[u]);
         for (int o = 0; o < NO[u]; ++o) {
             const int order = du.order + (du.cplx ? o / 2 : o);
             const int part = du.cplx ? (o & 1) : 0;
