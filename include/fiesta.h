@@ -41,6 +41,7 @@ extern "C" {
 #define FIESTA_FP64          0  /* all arithmetic in binary64 */
 #define FIESTA_FP32          1  /* integrand body in binary32; map, Jacobian, sums and grid in binary64 */
 #define FIESTA_AUTO          2  /* per unit: binary32 where a probe against binary64 stays within budget */
+#define FIESTA_DD            3  /* fiesta_eval_batch only: every point in double-double (about 106 bits) */
 
 #define FIESTA_NBINS       128  /* Vegas bins per coordinate */
 #define FIESTA_MAX_DIM       8  /* largest integration dimension */
@@ -102,7 +103,11 @@ typedef struct {
     int32_t no_graph;         /* nonzero: launch directly instead of replaying the iteration loop as a
                                  CUDA graph (captured on the first call, reused while the call's
                                  parameters are unchanged) */
-    int32_t reserved[3];
+    int32_t reserved;
+    double small_x;           /* extended precision near the boundary (the paper's mixed mode, Sec. 4.6,
+                                 SmallX): > 0 evaluates every binary64 point with a coordinate
+                                 below small_x in double-double; 0 = off.  Units with complex
+                                 results are rejected when it is set. */
 } fiesta_options;
 
 typedef struct {
@@ -131,6 +136,7 @@ typedef struct {
                                  complex unit's (re, im) pair counting as one */
     int32_t threads[2];       /* block size used for binary64 [0] and binary32 [1] */
     int32_t points_per_thread[2];
+    int64_t points_ext;       /* points evaluated in double-double (small_x) */
 } fiesta_stats;
 
 typedef struct fiesta_ctx fiesta_ctx;
@@ -165,9 +171,10 @@ int fiesta_integrate(fiesta_ctx *ctx, const fiesta_options *opt, double *value, 
 /*
  * Evaluate unit `unit` at n points: x is n*dim coordinates in (0,1), row-major,
  * f receives n*n_out values (row-major: the unit's results per point).  x and f are both host or both device pointers (the
- * library detects which).  precision is FIESTA_FP64 or FIESTA_FP32.  This is
- * the per-point hook, the counterpart of the paper's justEvaluate integrator
- * (Sec. 4.4).  Errors: FIESTA_E_INVALID, FIESTA_E_CUDA.
+ * library detects which).  precision is FIESTA_FP64, FIESTA_FP32 or FIESTA_DD
+ * (double-double arithmetic, results rounded to binary64; not for complex
+ * units).  This is the per-point hook, the counterpart of the paper's
+ * justEvaluate integrator (Sec. 4.4).  Errors: FIESTA_E_INVALID, FIESTA_E_CUDA.
  */
 int fiesta_eval_batch(fiesta_ctx *ctx, int64_t unit, int32_t precision, const double *x, int64_t n,
                       double *f);

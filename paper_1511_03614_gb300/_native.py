@@ -10,7 +10,7 @@ FIESTA_OK = 0
 ERRORS = {-1: "FIESTA_E_INVALID", -2: "FIESTA_E_NOMEM", -3: "FIESTA_E_CUDA",
           -4: "FIESTA_E_TIMEOUT", -5: "FIESTA_E_NONFINITE"}
 RNG = {"philox": 0, "sobol": 1}
-PRECISION = {"fp64": 0, "fp32": 1, "auto": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "auto": 2, "dd": 3}
 NBINS = 128
 MAX_DIM = 8
 FLOW_PARAMS = 4 * (16 * 64 + 64 + 64 * 64 + 64 + 64 * 16 + 16)
@@ -38,7 +38,7 @@ class Options(C.Structure):
                 ("unit_end", C.c_int64), ("timeout_ms", C.c_int64), ("threads", C.c_int32),
                 ("reset_grid", C.c_int32), ("iter_offset", C.c_int32), ("points_per_thread", C.c_int32),
                 ("probe_points", C.c_int64), ("fp32_budget", C.c_double), ("no_graph", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("reserved", C.c_int32), ("small_x", C.c_double)]
 
 
 class UnitResult(C.Structure):
@@ -51,7 +51,7 @@ class Stats(C.Structure):
     _fields_ = [("gpu_ms", C.c_double), ("eval_ms", C.c_double), ("points", C.c_int64),
                 ("points_per_s", C.c_double), ("kernels_launched", C.c_int32), ("eval_launches", C.c_int32),
                 ("units_fp32", C.c_int64), ("unit_points", C.c_int64), ("threads", C.c_int32 * 2),
-                ("points_per_thread", C.c_int32 * 2)]
+                ("points_per_thread", C.c_int32 * 2), ("points_ext", C.c_int64)]
 
 
 class CuhreOptions(C.Structure):

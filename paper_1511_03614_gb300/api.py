@@ -98,7 +98,7 @@ class Integrator:
     def integrate(self, n_iter=10, points=100_000, seed=1, rng="philox", precision="fp64", adapt=True,
                   alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
                   iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
-                  probe_points=0, fp32_budget=0.0, graph=True):
+                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0):
         lo = min(u.order for u in self.prep.units)
         hi = max(u.order + _n_orders(u) - 1 for u in self.prep.units)
         nord = hi - lo + 1
@@ -106,7 +106,8 @@ class Integrator:
         opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(adapt), int(points),
                         int(seed) & 0xFFFFFFFFFFFFFFFF, float(alpha), int(bool(skip_first)), lo, int(b), int(e),
                         int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset),
-                        int(points_per_thread), int(probe_points), float(fp32_budget), int(not graph))
+                        int(points_per_thread), int(probe_points), float(fp32_budget), int(not graph), 0,
+                        float(small_x))
         val = (C.c_double * nord)()
         err = (C.c_double * nord)()
         per = (N.UnitResult * sum(u.n_out for u in self.prep.units[b:e]))()
@@ -126,7 +127,7 @@ class Integrator:
         stats = dict(gpu_ms=st.gpu_ms, eval_ms=st.eval_ms, points=st.points, points_per_s=st.points_per_s,
                      kernels_launched=st.kernels_launched, eval_launches=st.eval_launches,
                      units_fp32=st.units_fp32, unit_points=st.unit_points, threads=tuple(st.threads),
-                     points_per_thread=tuple(st.points_per_thread))
+                     points_per_thread=tuple(st.points_per_thread), points_ext=st.points_ext)
         res = Result(values, errors, pu, stats)
         if assemble_result and units is None:
             res.assembled, res.assembled_errors = assemble(self.prep, values, errors)
