@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fuse", type=int, default=1, help="1: one unit per sector carrying all its eps orders")
-    ap.add_argument("--forms", default="fp64,auto,fp32,flow_fp32,cuhre_fp64",
+    ap.add_argument("--forms", default="fp64,auto,fp32,fp64_alloc,auto_alloc,flow_fp32,cuhre_fp64",
                     help="tta mode: comma-separated forms to run")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "tta"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
@@ -415,7 +415,8 @@ def _num(z):
 
 def run_tta(args):
     """GPU-seconds to the target relative error per eps order: plain binary64 Vegas
-    against the per-unit mixed precision policy and binary32, same GPU, same points."""
+    against the per-unit mixed precision policy, binary32, variance-driven point
+    allocation across units (*_alloc), the learned flow and the cubature."""
     import torch
     from paper_1511_03614_gb300 import Integrator
     from paper_1511_03614_gb300.api import run_to_accuracy
@@ -426,18 +427,20 @@ def run_tta(args):
            "units": len(prep.units), "runs": {}}
     from paper_1511_03614_gb300._native import FiestaError
     forms = set(args.forms.split(","))
-    for prec in ("fp64", "auto", "fp32"):
-        if prec not in forms:
+    for form in ("fp64", "auto", "fp32", "fp64_alloc", "auto_alloc", "fp32_alloc"):
+        if form not in forms:
             continue
+        prec = form.split("_")[0]
         integ = Integrator(prep)
         try:
             integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
-            r = run_to_accuracy(integ, target=args.target, points=pts, precision=prec, max_iters=400)
+            r = run_to_accuracy(integ, target=args.target, points=pts, precision=prec, max_iters=400,
+                                allocate=form.endswith("_alloc"))
         except FiestaError as e:
-            out["runs"][prec] = {"error": str(e)}
+            out["runs"][form] = {"error": str(e)}
             integ.close()
             continue
-        out["runs"][prec] = {"gpu_s": r["gpu_s"], "points": r["points"], "iterations": r["iterations"],
+        out["runs"][form] = {"gpu_s": r["gpu_s"], "points": r["points"], "iterations": r["iterations"],
                              "converged": r["converged"],
                              "values": {str(n): [_num(r["values"][n]), _num(r["errors"][n])] for n in r["values"]}}
         integ.close()

@@ -108,6 +108,11 @@ typedef struct {
                                  SmallX): > 0 evaluates every binary64 point with a coordinate
                                  below small_x in double-double; 0 = off.  Units with complex
                                  results are rejected when it is set. */
+    const int64_t *unit_points;  /* nullable host array, one entry per unit of the slice: points per
+                                 iteration of that unit (>= 2; <= 2^32 with Sobol), replacing
+                                 points_per_iter (which still sizes the autotuner's trials).  Lets a
+                                 caller spend points where the variance is (see the binding's
+                                 run_to_accuracy); the point streams do not depend on it. */
 } fiesta_options;
 
 typedef struct {

@@ -98,7 +98,7 @@ class Integrator:
     def integrate(self, n_iter=10, points=100_000, seed=1, rng="philox", precision="fp64", adapt=True,
                   alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
                   iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
-                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0):
+                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0, unit_points=None):
         lo = min(u.order for u in self.prep.units)
         hi = max(u.order + _n_orders(u) - 1 for u in self.prep.units)
         nord = hi - lo + 1
@@ -108,6 +108,11 @@ class Integrator:
                         int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset),
                         int(points_per_thread), int(probe_points), float(fp32_budget), int(not graph), 0,
                         float(small_x))
+        if unit_points is not None:
+            upts = np.ascontiguousarray(unit_points, dtype=np.int64)
+            if upts.shape != (e - b,):
+                raise ValueError("unit_points needs one entry per unit of the slice")
+            opt.unit_points = upts.ctypes.data_as(C.POINTER(C.c_int64))
         val = (C.c_double * nord)()
         err = (C.c_double * nord)()
         per = (N.UnitResult * sum(u.n_out for u in self.prep.units[b:e]))()
@@ -385,9 +390,48 @@ def load_checkpoint(path, integ=None):
     return state
 
 
+def allocate_points(prep, sig, n_used, values, target, floor, points, lo_frac=0.01, hi_mult=64):
+    """Points per unit for the next iterations: Neyman allocation for the assembled
+    series.  Unit u's per-point standard deviation of its eps-order-K integral is
+    s_uK = sigma_uK sqrt(points used so far); its share of the error of result order n
+    is sum_K |c_(n-K)| s_uK / sqrt(N_u) (c the prefactor series); with
+    B_u = max_n (sum_K |c_(n-K)| s_uK / tau_n)^2 and a cost per point w_u (program
+    length + map), N_u proportional to sqrt(B_u / w_u) minimises the cost at a given
+    error.  The total cost equals that of ``points`` per unit; each N_u is clamped to
+    [lo_frac * points, hi_mult * points]."""
+    q, coeffs = prep.prefactor
+    R = assemble(prep, values, {K: 0.0 for K in values})[0]
+    big = max(abs(v) for v in R.values())
+    tau = {n: target * max(abs(R[n]), floor * big) for n in R}
+    s = {}
+    k = 0
+    for ui, u in enumerate(prep.units):
+        for o in range(u.n_out):
+            K, part = _record_key(u, o)
+            s.setdefault(ui, {}).setdefault(K, 0.0)
+            s[ui][K] += (sig[k] ** 2) * n_used[ui]
+            k += 1
+    cost = np.array([len(u.program.code) + 4 * u.dim + 8 for u in prep.units], dtype=float)
+    B = np.zeros(len(prep.units))
+    for ui in range(len(prep.units)):
+        for n, t in tau.items():
+            acc = 0.0
+            for K, s2 in s[ui].items():
+                i = n - K + q
+                if 0 <= i < len(coeffs):
+                    acc += abs(float(coeffs[i])) * math.sqrt(s2)
+            B[ui] = max(B[ui], (acc / t) ** 2)
+    wgt = np.sqrt(np.maximum(B, 0.0) / cost)
+    if not np.any(wgt > 0):
+        return np.full(len(prep.units), int(points), dtype=np.int64)
+    N = wgt * (points * cost.sum()) / float(np.sum(wgt * cost))
+    N = np.clip(N, max(2, lo_frac * points), hi_mult * points)
+    return np.maximum(N.astype(np.int64), 2)
+
+
 def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_iters=200, seed=1,
                     precision="fp64", rng="philox", floor=1e-2, skip_first=1, checkpoint=None, resume=None,
-                    stop_after=None):
+                    stop_after=None, allocate=False):
     """Vegas until every eps order of the assembled result has sigma <= target * max(|R|, floor * max|R|).
 
     Iterations are combined per unit with inverse-variance weights across calls
@@ -398,10 +442,14 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
     streams (iteration numbers continue); ``stop_after`` ends after that many
     iterations (to emulate an interrupted job).  Returns a dict with the GPU
     seconds (the library's device time over all calls), the points, the
-    iterations and the final values and errors.
+    iterations and the final values and errors.  ``allocate`` spends the points of
+    every call after the first where the variance is (``allocate_points``) instead of
+    evenly; the total points per iteration stay nu * points.
     """
     prep = integ.prep
     recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
+    unit_pts = None
+    n_used = np.zeros(len(prep.units))
     nu = len(recs)
     sw = np.zeros(nu)
     swi = np.zeros(nu)
@@ -415,9 +463,12 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
         gpu_ms, points_done, seed = st["gpu_ms"], st["points_done"], st["seed"]
     while it < max_iters:
         r = integ.integrate(n_iter=iters_per_call, points=points, seed=seed, rng=rng, precision=precision,
-                            adapt=2, reset_grid=(it == 0), iter_offset=it, assemble_result=False)
+                            adapt=2, reset_grid=(it == 0), iter_offset=it, assemble_result=False,
+                            unit_points=unit_pts)
         gpu_ms += r.stats["gpu_ms"]
         points_done += r.stats["unit_points"]
+        used_now = np.full(len(prep.units), float(points)) if unit_pts is None else unit_pts.astype(float)
+        n_used += used_now * sum(1 for j in range(iters_per_call) if it + j >= skip_first)
         for k, (unit, o) in enumerate(recs):
             m, v = integ.iterations(unit, iters_per_call, o)
             for j in range(iters_per_call):
@@ -451,6 +502,8 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
                    unit_values=val.copy(), unit_sigmas=sig.copy())
         if ok or (stop_after is not None and it >= stop_after):
             break
+        if allocate and np.all(n_used > 0):
+            unit_pts = allocate_points(prep, sig, n_used, values, target, floor, points)
     return res
 
 
