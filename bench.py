@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--fuse", type=int, default=1, help="1: one unit per sector carrying all its eps orders")
     ap.add_argument("--forms", default="fp64,auto,fp32,fp64_alloc,auto_alloc,flow_fp32,cuhre_fp64",
                     help="tta mode: comma-separated forms to run")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "tta"],
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
     ap.add_argument("--target", type=float, default=1e-4)
     return ap.parse_args()
@@ -482,12 +482,43 @@ def run_tta(args):
     print(json.dumps(out))
 
 
+def run_cuhre(args):
+    """Throughput of the adaptive cubature: one fiesta_cuhre call per step on the fused
+    units of the workload at relative tolerance --target, reported as integrand
+    evaluations per second (a fused unit's evaluation yields all its orders), with the
+    evaluation kernels' share of the device time.  Not the headline line."""
+    import torch
+    from paper_1511_03614_gb300 import Integrator
+    torch.cuda.set_device(0)
+    prep = prepared(args.workload, fuse=True)
+    integ = Integrator(prep)
+    for _ in range(args.warmup):
+        integ.cuhre(rel_tol=args.target)
+    gpu_ms = eval_ms = 0.0
+    pts = 0
+    res = None
+    for _ in range(args.steps):
+        res = integ.cuhre(rel_tol=args.target)
+        gpu_ms += res.stats["gpu_ms"]
+        eval_ms += res.stats["eval_ms"]
+        pts += res.stats["points"]
+    print(json.dumps({"mode": "cuhre", "workload": args.workload, "rel_tol": args.target, "steps": args.steps,
+                      "evaluations_per_s": pts / (gpu_ms * 1e-3), "eval_kernel_share": eval_ms / gpu_ms,
+                      "gpu_ms_per_step": gpu_ms / args.steps, "evaluations_per_step": pts // args.steps,
+                      "regions": sum({d["unit"]: d["n_regions"] for d in res.per_unit}.values()),
+                      "converged_units": sum(d["converged"] for d in res.per_unit),
+                      "results": {str(n): [_num(res.assembled[n]), _num(res.assembled_errors[n])]
+                                  for n in res.assembled}}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "tta":
         run_tta(args)
+    elif args.mode == "cuhre":
+        run_cuhre(args)
     else:
         run_ours(args)
 

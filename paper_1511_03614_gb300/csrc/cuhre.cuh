@@ -15,22 +15,23 @@
 // slice.  The live list is kept sorted by unit (children replace their parent in
 // place order), so each unit owns one contiguous run of regions and every
 // per-unit step is a fixed-order block reduction.  Per pass:
-//   k_cuhre_points  one thread per (region, rule point): the point, the
-//                   bytecode interpreter, the n_out values into a point buffer;
-//   k_cuhre_rule    one warp per region: I7, I5, |I7 - I5| per result, split axis;
+//   k_cuhre_eval    one block per batch of a unit's regions (about CU_ITEM_PTS rule
+//                   points): one thread per (region, rule point) runs the bytecode
+//                   interpreter into a shared-memory buffer, then one warp per region
+//                   forms I7, I5, |I7 - I5| per result and the split axis;
 //   k_cuhre_decide  one block per unit: sums over its live regions, tolerances,
 //                   convergence; regions within their volume's share of the
 //                   tolerance are frozen (their sums added to the unit's frozen
 //                   totals), the others flagged for splitting;
 //   k_cuhre_split   one block per unit: block scan of the flags, children written
 //                   to the next live list.
-// The host reads the per-unit split counts once per pass to size the next list.
+// The host reads the per-unit split counts once per pass to size the next list and
+// uploads two prefix tables of nu + 1 entries (regions and blocks per unit).
 
 namespace {
 
 constexpr int CU_STRIDE = FIESTA_MAX_DIM;          // doubles per region centre / half-width
-constexpr int CU_PPT = 4;                          // points per thread per work item
-constexpr int64_t CU_FBUF_MAX = int64_t(1) << 26;  // point-buffer doubles per chunk (512 MB)
+constexpr int CU_ITEM_PTS = 512;                   // rule points per block (a batch of whole regions)
 
 struct CuRule {
     double w[5];     // degree-7 weights, volume-1 region
@@ -96,16 +97,8 @@ __device__ __forceinline__ double cu_gen(int p, int j, int n, const CuConsts &K)
     return ((t >> (n - 1 - j)) & 1) ? -K.lam5 : K.lam5;
 }
 
-struct CuWork {
-    int32_t u;        // unit position in the slice
-    int32_t pad;
-    int64_t r0;       // first region of the unit's run in this chunk (live-list index)
-    int64_t q0, q1;   // points [q0, q1) of the run handled by this item
-    int64_t fbase;    // point-buffer offset (doubles) of the run's first point
-};
-
 struct CuSmem {
-    size_t code, cons, logtab, x, slots, total;
+    size_t code, cons, logtab, x, slots, f, total;
 };
 
 __host__ __device__ inline CuSmem cu_smem(int max_instr, int max_const, int max_slots, int threads) {
@@ -116,9 +109,13 @@ __host__ __device__ inline CuSmem cu_smem(int max_instr, int max_const, int max_
     L.logtab = off; off = align16(off + sizeof(double) * LOGTAB_DOUBLES);
     L.x = off; off = align16(off + sizeof(double) * MAXD * threads);
     L.slots = off; off = align16(off + sizeof(double) * max_slots * threads);
+    L.f = off; off = align16(off + sizeof(double) * CU_ITEM_PTS * MAXO);
     L.total = off;
     return L;
 }
+
+// Regions per block for rule points P: whole regions, about CU_ITEM_PTS points.
+__host__ __device__ inline int cu_batch(int P) { return P >= CU_ITEM_PTS ? 1 : CU_ITEM_PTS / P; }
 
 __global__ void k_cuhre_init(int64_t nu, double *rc, double *rh, int32_t *runit) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -128,16 +125,28 @@ __global__ void k_cuhre_init(int64_t nu, double *rc, double *rh, int32_t *runit)
     if (i % CU_STRIDE == 0) runit[i / CU_STRIDE] = static_cast<int32_t>(i / CU_STRIDE);
 }
 
-__global__ void __launch_bounds__(256) k_cuhre_points(const DevUnit *__restrict__ units, int64_t unit_begin,
-                                                      const uint32_t *__restrict__ code,
-                                                      const double *__restrict__ cons64,
-                                                      const double *__restrict__ logtab,
-                                                      const CuWork *__restrict__ work, const double *__restrict__ rc,
-                                                      const double *__restrict__ rh, double *__restrict__ fbuf,
-                                                      CuConsts K, int max_instr, int max_const, int max_slots) {
+// Block = item: a batch of consecutive regions of one unit (item_off: first item of
+// each unit position, reg_off: its first live region).
+__global__ void __launch_bounds__(256) k_cuhre_eval(const DevUnit *__restrict__ units, int64_t unit_begin,
+                                                    const uint32_t *__restrict__ code,
+                                                    const double *__restrict__ cons64,
+                                                    const double *__restrict__ logtab,
+                                                    const int64_t *__restrict__ item_off,
+                                                    const int64_t *__restrict__ reg_off, int64_t n_pos,
+                                                    const double *__restrict__ rc, const double *__restrict__ rh,
+                                                    double *__restrict__ rval, double *__restrict__ rerr,
+                                                    int32_t *__restrict__ raxis, CuConsts K, int max_instr,
+                                                    int max_const, int max_slots) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const CuWork w = work[blockIdx.x];
-    const DevUnit u = units[unit_begin + w.u];
+    const int64_t item = blockIdx.x;
+    int64_t lo = 0, hi = n_pos;                       // item_off[lo] <= item < item_off[lo + 1]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (item_off[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    const int64_t up = lo;
+    const DevUnit u = units[unit_begin + up];
     const int nt = blockDim.x, tid = threadIdx.x;
     const CuSmem L = cu_smem(max_instr, max_const, max_slots, nt);
     uint32_t *s_code = reinterpret_cast<uint32_t *>(smem + L.code);
@@ -145,104 +154,96 @@ __global__ void __launch_bounds__(256) k_cuhre_points(const DevUnit *__restrict_
     double *s_logtab = reinterpret_cast<double *>(smem + L.logtab);
     double *s_x = reinterpret_cast<double *>(smem + L.x);
     double *s_slots = reinterpret_cast<double *>(smem + L.slots);
+    double *s_f = reinterpret_cast<double *>(smem + L.f);
     for (int i = tid; i < LOGTAB_DOUBLES; i += nt) s_logtab[i] = logtab[i];
     for (int i = tid; i < u.n_instr; i += nt) s_code[i] = code[u.code_off + i];
     for (int i = tid; i < u.n_const; i += nt) s_cons[i] = cons64[u.const_off + i];
     __syncthreads();
     const int n = cu_n(u.dim), P = cu_points(n), no = u.n_out;
-    for (int64_t q = w.q0 + tid; q < w.q1; q += nt) {
-        const int64_t r = w.r0 + q / P;
-        const int p = static_cast<int>(q % P);
+    const int64_t r0 = reg_off[up] + (item - item_off[up]) * cu_batch(P);
+    const int nr = static_cast<int>(min(static_cast<int64_t>(cu_batch(P)), reg_off[up + 1] - r0));
+    const int npts = nr * P;
+    for (int q = tid; q < npts; q += nt) {
+        const int64_t r = r0 + q / P;
+        const int p = q % P;
         const double *c = rc + r * CU_STRIDE;
         const double *h = rh + r * CU_STRIDE;
         for (int j = 0; j < u.dim; ++j) s_x[j * nt + tid] = __dadd_rn(c[j], __dmul_rn(cu_gen(p, j, n, K), h[j]));
         (void)interpret<double>(s_code, u.n_instr, s_cons, s_slots + tid, s_x + tid, nt, u.out_slot, s_logtab);
-        double *out = fbuf + w.fbase + q * no;
-        for (int o = 0; o < no; ++o) out[o] = s_slots[tid + u.outs[o] * nt];
+        for (int o = 0; o < no; ++o) s_f[q * no + o] = s_slots[tid + u.outs[o] * nt];
     }
-}
-
-// One warp per region of [R0, R1).
-__global__ void __launch_bounds__(256) k_cuhre_rule(const DevUnit *__restrict__ units, int64_t unit_begin,
-                                                    const int32_t *__restrict__ runit, const double *__restrict__ rh,
-                                                    int64_t R0, int64_t R1, const int64_t *__restrict__ run_r0,
-                                                    const int64_t *__restrict__ run_fbase,
-                                                    const double *__restrict__ fbuf, double *__restrict__ rval,
-                                                    double *__restrict__ rerr, int32_t *__restrict__ raxis,
-                                                    CuConsts K) {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = R0 + (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
-    if (r >= R1) return;                       // r is uniform over the warp
-    const int up = runit[r];
-    const DevUnit u = units[unit_begin + up];
-    const int n = cu_n(u.dim), P = cu_points(n), no = u.n_out;
-    const double *f = fbuf + run_fbase[up] + (r - run_r0[up]) * static_cast<int64_t>(P) * no;
-    const double *h = rh + r * CU_STRIDE;
+    __syncthreads();
+    const int lane = tid & 31, nw = nt >> 5;
     const CuRule &W = K.rule[n];
     const int e1 = 2 * n, e2 = 4 * n, e3 = 4 * n + 2 * n * (n - 1);
-    double a7[MAXO], a5[MAXO];
+    for (int rr = tid >> 5; rr < nr; rr += nw) {
+        const int64_t r = r0 + rr;
+        const double *f = s_f + rr * P * no;
+        const double *h = rh + r * CU_STRIDE;
+        double a7[MAXO], a5[MAXO];
 #pragma unroll
-    for (int o = 0; o < MAXO; ++o) a7[o] = a5[o] = 0.0;
-    for (int p = lane; p < P; p += 32) {
-        double w7, w5;
-        if (p == 0) { w7 = W.w[0]; w5 = W.v[0]; }
-        else if (p <= e1) { w7 = W.w[1]; w5 = W.v[1]; }
-        else if (p <= e2) { w7 = W.w[2]; w5 = W.v[2]; }
-        else if (p <= e3) { w7 = W.w[3]; w5 = W.v[3]; }
-        else { w7 = W.w[4]; w5 = 0.0; }
+        for (int o = 0; o < MAXO; ++o) a7[o] = a5[o] = 0.0;
+        for (int p = lane; p < P; p += 32) {
+            double w7, w5;
+            if (p == 0) { w7 = W.w[0]; w5 = W.v[0]; }
+            else if (p <= e1) { w7 = W.w[1]; w5 = W.v[1]; }
+            else if (p <= e2) { w7 = W.w[2]; w5 = W.v[2]; }
+            else if (p <= e3) { w7 = W.w[3]; w5 = W.v[3]; }
+            else { w7 = W.w[4]; w5 = 0.0; }
 #pragma unroll
-        for (int o = 0; o < MAXO; ++o)
-            if (o < no) {
-                const double y = f[static_cast<int64_t>(p) * no + o];
-                a7[o] = fma(w7, y, a7[o]);
-                a5[o] = fma(w5, y, a5[o]);
+            for (int o = 0; o < MAXO; ++o)
+                if (o < no) {
+                    const double y = f[p * no + o];
+                    a7[o] = fma(w7, y, a7[o]);
+                    a5[o] = fma(w5, y, a5[o]);
+                }
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1)
+#pragma unroll
+            for (int o = 0; o < MAXO; ++o)
+                if (o < no) {
+                    a7[o] += __shfl_xor_sync(0xffffffffu, a7[o], s);
+                    a5[o] += __shfl_xor_sync(0xffffffffu, a5[o], s);
+                }
+        // fourth differences: lane j < n for coordinate j
+        double D = -1.0, hj = 0.0;
+        int jj = lane;
+        if (lane < n) {
+            D = 0.0;
+            hj = h[lane];
+            for (int o = 0; o < no; ++o) {
+                const double f0 = f[o];
+                const double y2p = f[(1 + 2 * lane) * no + o];
+                const double y2m = f[(2 + 2 * lane) * no + o];
+                const double y3p = f[(1 + e1 + 2 * lane) * no + o];
+                const double y3m = f[(2 + e1 + 2 * lane) * no + o];
+                const double t2 = __dsub_rn(__dadd_rn(y2p, y2m), __dmul_rn(2.0, f0));
+                const double t3 = __dsub_rn(__dadd_rn(y3p, y3m), __dmul_rn(2.0, f0));
+                D = __dadd_rn(D, fabs(__dsub_rn(t2, __dmul_rn(K.ratio, t3))));
             }
-    }
+        }
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1)
-#pragma unroll
-        for (int o = 0; o < MAXO; ++o)
-            if (o < no) {
-                a7[o] += __shfl_xor_sync(0xffffffffu, a7[o], s);
-                a5[o] += __shfl_xor_sync(0xffffffffu, a5[o], s);
+        for (int s = 16; s > 0; s >>= 1) {
+            const double D2 = __shfl_xor_sync(0xffffffffu, D, s);
+            const double h2 = __shfl_xor_sync(0xffffffffu, hj, s);
+            const int j2 = __shfl_xor_sync(0xffffffffu, jj, s);
+            if (D2 > D || (D2 == D && (h2 > hj || (h2 == hj && j2 < jj)))) {
+                D = D2;
+                hj = h2;
+                jj = j2;
             }
-    // fourth differences: lane j < n for coordinate j
-    double D = -1.0, hj = 0.0;
-    int jj = lane;
-    if (lane < n) {
-        D = 0.0;
-        hj = h[lane];
-        for (int o = 0; o < no; ++o) {
-            const double f0 = f[o];
-            const double y2p = f[static_cast<int64_t>(1 + 2 * lane) * no + o];
-            const double y2m = f[static_cast<int64_t>(2 + 2 * lane) * no + o];
-            const double y3p = f[static_cast<int64_t>(1 + e1 + 2 * lane) * no + o];
-            const double y3m = f[static_cast<int64_t>(2 + e1 + 2 * lane) * no + o];
-            const double t2 = __dsub_rn(__dadd_rn(y2p, y2m), __dmul_rn(2.0, f0));
-            const double t3 = __dsub_rn(__dadd_rn(y3p, y3m), __dmul_rn(2.0, f0));
-            D = __dadd_rn(D, fabs(__dsub_rn(t2, __dmul_rn(K.ratio, t3))));
         }
-    }
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        const double D2 = __shfl_xor_sync(0xffffffffu, D, s);
-        const double h2 = __shfl_xor_sync(0xffffffffu, hj, s);
-        const int j2 = __shfl_xor_sync(0xffffffffu, jj, s);
-        if (D2 > D || (D2 == D && (h2 > hj || (h2 == hj && j2 < jj)))) {
-            D = D2;
-            hj = h2;
-            jj = j2;
+        if (lane == 0) {
+            double V = 1.0;
+            for (int j = 0; j < n; ++j) V *= 2.0 * h[j];
+            for (int o = 0; o < no; ++o) {
+                const double i7 = V * a7[o], i5 = V * a5[o];
+                rval[r * MAXO + o] = i7;
+                rerr[r * MAXO + o] = fabs(i7 - i5);
+            }
+            raxis[r] = jj;
         }
-    }
-    if (lane == 0) {
-        double V = 1.0;
-        for (int j = 0; j < n; ++j) V *= 2.0 * h[j];
-        for (int o = 0; o < no; ++o) {
-            const double i7 = V * a7[o], i5 = V * a5[o];
-            rval[r * MAXO + o] = i7;
-            rerr[r * MAXO + o] = fabs(i7 - i5);
-        }
-        raxis[r] = jj;
     }
 }
 
@@ -437,12 +438,8 @@ struct CuhreState {
     int32_t *raxis = nullptr;
     uint8_t *rflag = nullptr;
     int64_t reg_cap = 0;
-    double *fbuf = nullptr;
-    int64_t fbuf_cap = 0;
-    CuWork *work = nullptr;
-    int64_t work_cap = 0;
     // per unit of the slice
-    int64_t *reg_off = nullptr, *new_off = nullptr, *run_r0 = nullptr, *run_fbase = nullptr, *nsplit = nullptr;
+    int64_t *reg_off = nullptr, *new_off = nullptr, *item_off = nullptr, *nsplit = nullptr;
     double *frz_v = nullptr, *frz_e = nullptr, *tot_v = nullptr, *tot_e = nullptr, *fp_v = nullptr, *fp_e = nullptr;
     int32_t *conv = nullptr, *bad = nullptr;
     int64_t unit_cap = 0;
@@ -455,20 +452,6 @@ struct CuhreState {
 void cuhre_state_delete(CuhreState *s) { delete s; }   // device arrays belong to the context
 
 namespace {
-
-template <typename T> int cu_grow(fiesta_ctx *c, T *&ptr, int64_t &cap, int64_t need) {
-    if (need <= cap && ptr) return FIESTA_OK;
-    int64_t n = std::max<int64_t>(need, cap * 2);
-    n = std::max<int64_t>(n, 64);
-    c->dfree(ptr);
-    ptr = static_cast<T *>(c->dmalloc(sizeof(T) * n));
-    if (!ptr) {
-        cap = 0;
-        return fail(FIESTA_E_NOMEM, "fiesta_cuhre: device allocation failed");
-    }
-    cap = n;
-    return FIESTA_OK;
-}
 
 int cu_grow_list(fiesta_ctx *c, CuhreState &S, int which, int64_t need) {
     if (need <= S.list_cap[which] && S.rc[which]) return FIESTA_OK;
@@ -508,7 +491,7 @@ int cu_grow_regions(fiesta_ctx *c, CuhreState &S, int64_t need) {
 
 int cu_grow_units(fiesta_ctx *c, CuhreState &S, int64_t nu) {
     if (nu <= S.unit_cap && S.reg_off) return FIESTA_OK;
-    void **ptrs[] = {(void **)&S.reg_off, (void **)&S.new_off, (void **)&S.run_r0, (void **)&S.run_fbase,
+    void **ptrs[] = {(void **)&S.reg_off, (void **)&S.new_off, (void **)&S.item_off,
                      (void **)&S.nsplit, (void **)&S.frz_v, (void **)&S.frz_e, (void **)&S.tot_v,
                      (void **)&S.tot_e, (void **)&S.fp_v, (void **)&S.fp_e, (void **)&S.conv, (void **)&S.bad};
     for (void **p : ptrs) {
@@ -518,8 +501,7 @@ int cu_grow_units(fiesta_ctx *c, CuhreState &S, int64_t nu) {
     const int64_t n = nu + 1;
     S.reg_off = static_cast<int64_t *>(c->dmalloc(sizeof(int64_t) * n));
     S.new_off = static_cast<int64_t *>(c->dmalloc(sizeof(int64_t) * n));
-    S.run_r0 = static_cast<int64_t *>(c->dmalloc(sizeof(int64_t) * n));
-    S.run_fbase = static_cast<int64_t *>(c->dmalloc(sizeof(int64_t) * n));
+    S.item_off = static_cast<int64_t *>(c->dmalloc(sizeof(int64_t) * n));
     S.nsplit = static_cast<int64_t *>(c->dmalloc(sizeof(int64_t) * n));
     S.frz_v = static_cast<double *>(c->dmalloc(sizeof(double) * MAXO * n));
     S.frz_e = static_cast<double *>(c->dmalloc(sizeof(double) * MAXO * n));
@@ -565,7 +547,7 @@ int fiesta_cuhre(fiesta_ctx *c, const fiesta_cuhre_options *opt, double *value, 
     const SliceInfo si = slice_info(c, b, e);
     const CuConsts K = cu_consts();
     const CuSmem L = cu_smem(si.max_instr, si.max_const, si.max_slots, threads);
-    if (cudaFuncSetAttribute(k_cuhre_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_cuhre_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
         return fail(FIESTA_E_NOMEM, "fiesta_cuhre: shared memory for these programs exceeds the device limit");
     int rc = cu_grow_units(c, S, nu);
     if (!rc) rc = cu_grow_list(c, S, 0, nu);
@@ -603,8 +585,7 @@ int fiesta_cuhre(fiesta_ctx *c, const fiesta_cuhre_options *opt, double *value, 
     int64_t frozen_total = 0;
     bool timed_out = false;
     const auto t_start = std::chrono::steady_clock::now();
-    std::vector<CuWork> work;
-    std::vector<int64_t> h_r0(nu), h_fb(nu);
+    std::vector<int64_t> item_off(nu + 1);
     for (int pass = 0;; ++pass) {
         off[0] = 0;
         for (int64_t k = 0; k < nu; ++k) off[k + 1] = off[k] + nreg[k];
@@ -613,66 +594,20 @@ int fiesta_cuhre(fiesta_ctx *c, const fiesta_cuhre_options *opt, double *value, 
         rc = cu_grow_regions(c, S, live);
         if (rc) break;
         CUDA_TRY(cudaMemcpyAsync(S.reg_off, off.data(), sizeof(int64_t) * (nu + 1), cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaEventRecord(p0, st));
-        // chunks of whole regions whose point values fit the point buffer; a unit's
-        // run of regions may be cut between two chunks
-        int64_t ku = 0, rnext = 0;
-        while (rc == FIESTA_OK) {
-            while (ku < nu && rnext >= off[ku + 1]) ++ku;
-            if (ku >= nu) break;
-            const int64_t R0 = rnext, ka = ku;
-            int64_t kb = ku, used = 0;
-            work.clear();
-            while (ku < nu) {
-                if (rnext >= off[ku + 1]) {
-                    ++ku;
-                    continue;
-                }
-                const int64_t per = (int64_t)P[ku] * NO[ku];
-                const int64_t take = std::min<int64_t>(off[ku + 1] - rnext, (CU_FBUF_MAX - used) / per);
-                if (take <= 0) break;
-                h_r0[ku] = rnext;
-                h_fb[ku] = used;
-                kb = ku;
-                const int64_t pts = take * P[ku];
-                const int64_t step = (int64_t)threads * CU_PPT;
-                for (int64_t q = 0; q < pts; q += step) {
-                    CuWork w{};
-                    w.u = (int32_t)ku;
-                    w.r0 = rnext;
-                    w.q0 = q;
-                    w.q1 = std::min(pts, q + step);
-                    w.fbase = used;
-                    work.push_back(w);
-                }
-                used += take * per;
-                rnext += take;
-            }
-            const int64_t R1 = rnext;
-            if (R1 == R0) {
-                rc = fail(FIESTA_E_NOMEM, "fiesta_cuhre: one region's points exceed the point buffer");
-                break;
-            }
-            rc = cu_grow(c, S.fbuf, S.fbuf_cap, used);
-            if (!rc) rc = cu_grow(c, S.work, S.work_cap, (int64_t)work.size());
-            if (rc) break;
-            CUDA_TRY(cudaMemcpyAsync(S.work, work.data(), sizeof(CuWork) * work.size(), cudaMemcpyHostToDevice, st));
-            CUDA_TRY(cudaMemcpyAsync(S.run_r0 + ka, h_r0.data() + ka, sizeof(int64_t) * (kb - ka + 1),
-                                     cudaMemcpyHostToDevice, st));
-            CUDA_TRY(cudaMemcpyAsync(S.run_fbase + ka, h_fb.data() + ka, sizeof(int64_t) * (kb - ka + 1),
-                                     cudaMemcpyHostToDevice, st));
-            k_cuhre_points<<<(unsigned)work.size(), threads, L.total, st>>>(
-                c->d_units, b, c->d_code, c->d_cons64, c->d_logtab, S.work, S.rc[S.cur], S.rh[S.cur], S.fbuf, K,
-                si.max_instr, si.max_const, si.max_slots);
-            const int64_t nr = R1 - R0;
-            k_cuhre_rule<<<(unsigned)((nr * 32 + 255) / 256), 256, 0, st>>>(
-                c->d_units, b, S.runit[S.cur], S.rh[S.cur], R0, R1, S.run_r0, S.run_fbase, S.fbuf, S.rval, S.rerr,
-                S.raxis, K);
-            launches += 2;
-            eval_launches += 1;
-            CUDA_TRY(cudaGetLastError());
+        // blocks: per unit, batches of whole regions (cu_batch regions each)
+        item_off[0] = 0;
+        for (int64_t k = 0; k < nu; ++k) {
+            const int bt = cu_batch(P[k]);
+            item_off[k + 1] = item_off[k] + (nreg[k] + bt - 1) / bt;
         }
-        if (rc) break;
+        CUDA_TRY(cudaMemcpyAsync(S.item_off, item_off.data(), sizeof(int64_t) * (nu + 1), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaEventRecord(p0, st));
+        k_cuhre_eval<<<(unsigned)item_off[nu], threads, L.total, st>>>(
+            c->d_units, b, c->d_code, c->d_cons64, c->d_logtab, S.item_off, S.reg_off, nu, S.rc[S.cur],
+            S.rh[S.cur], S.rval, S.rerr, S.raxis, K, si.max_instr, si.max_const, si.max_slots);
+        launches += 1;
+        eval_launches += 1;
+        CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaEventRecord(p1, st));
         const bool final_pass = pass + 1 >= max_passes;
         CuDecideArgs A{};
@@ -814,7 +749,7 @@ int fiesta_cuhre(fiesta_ctx *c, const fiesta_cuhre_options *opt, double *value, 
         stats->eval_launches = eval_launches;
         stats->unit_points = unit_pts;
         stats->threads[0] = threads;
-        stats->points_per_thread[0] = CU_PPT;
+        stats->points_per_thread[0] = CU_ITEM_PTS / threads;
     }
     if (bad) return fail(FIESTA_E_NONFINITE, "fiesta_cuhre: a unit's estimate is not finite");
     if (timed_out) return fail(FIESTA_E_TIMEOUT, "fiesta_cuhre: time budget exceeded");
