@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
     ap.add_argument("--target", type=float, default=1e-4)
+    ap.add_argument("--max-iters", type=int, default=400, help="tta mode: Vegas iteration cap per form")
     return ap.parse_args()
 
 
@@ -416,7 +417,8 @@ def _num(z):
 def run_tta(args):
     """GPU-seconds to the target relative error per eps order: plain binary64 Vegas
     against the per-unit mixed precision policy, binary32, variance-driven point
-    allocation across units (*_alloc), the learned flow and the cubature."""
+    allocation across units (*_alloc), binary64 for the points near the boundary of
+    binary32 units (*_mixed: small_x = 1e-2), the learned flow and the cubature."""
     import torch
     from paper_1511_03614_gb300 import Integrator
     from paper_1511_03614_gb300.api import run_to_accuracy
@@ -427,15 +429,16 @@ def run_tta(args):
            "units": len(prep.units), "runs": {}}
     from paper_1511_03614_gb300._native import FiestaError
     forms = set(args.forms.split(","))
-    for form in ("fp64", "auto", "fp32", "fp64_alloc", "auto_alloc", "fp32_alloc"):
+    for form in ("fp64", "auto", "fp32", "fp64_alloc", "auto_alloc", "fp32_alloc", "auto_mixed",
+                 "auto_mixed_alloc"):
         if form not in forms:
             continue
         prec = form.split("_")[0]
         integ = Integrator(prep)
         try:
             integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
-            r = run_to_accuracy(integ, target=args.target, points=pts, precision=prec, max_iters=400,
-                                allocate=form.endswith("_alloc"))
+            r = run_to_accuracy(integ, target=args.target, points=pts, precision=prec, max_iters=args.max_iters,
+                                allocate=form.endswith("_alloc"), small_x=1e-2 if "_mixed" in form else 0.0)
         except FiestaError as e:
             out["runs"][form] = {"error": str(e)}
             integ.close()

@@ -431,7 +431,7 @@ def allocate_points(prep, sig, n_used, values, target, floor, points, lo_frac=0.
 
 def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_iters=200, seed=1,
                     precision="fp64", rng="philox", floor=1e-2, skip_first=1, checkpoint=None, resume=None,
-                    stop_after=None, allocate=False):
+                    stop_after=None, allocate=False, small_x=0.0):
     """Vegas until every eps order of the assembled result has sigma <= target * max(|R|, floor * max|R|).
 
     Iterations are combined per unit with inverse-variance weights across calls
@@ -444,7 +444,8 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
     seconds (the library's device time over all calls), the points, the
     iterations and the final values and errors.  ``allocate`` spends the points of
     every call after the first where the variance is (``allocate_points``) instead of
-    evenly; the total points per iteration stay nu * points.
+    evenly; the total points per iteration stay nu * points.  ``small_x`` promotes
+    points near the boundary one precision level (see Integrator.integrate).
     """
     prep = integ.prep
     recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
@@ -464,7 +465,7 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
     while it < max_iters:
         r = integ.integrate(n_iter=iters_per_call, points=points, seed=seed, rng=rng, precision=precision,
                             adapt=2, reset_grid=(it == 0), iter_offset=it, assemble_result=False,
-                            unit_points=unit_pts)
+                            unit_points=unit_pts, small_x=small_x)
         gpu_ms += r.stats["gpu_ms"]
         points_done += r.stats["unit_points"]
         used_now = np.full(len(prep.units), float(points)) if unit_pts is None else unit_pts.astype(float)

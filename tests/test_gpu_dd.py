@@ -118,3 +118,26 @@ def test_dd_rejects_complex_units():
         integ.eval_batch(0, np.full((4, integ.prep.units[0].dim), 0.5), "dd")
     with pytest.raises(FiestaError):
         integ.integrate(n_iter=1, points=1000, small_x=1e-6)
+
+
+def test_fp32_with_binary64_near_the_boundary():
+    """small_x with the binary32 body: points near the boundary run in binary64 (the
+    subtraction differences there stay binary64); results within errors of binary64,
+    the promoted points counted; on the double box the AUTO probe then accepts more
+    units for binary32 than without promotion."""
+    need_gpu()
+    integ = integrator("box")
+    r64 = integ.integrate(n_iter=5, points=200_000, seed=3)
+    r32 = integ.integrate(n_iter=5, points=200_000, seed=3, precision="fp32", small_x=1e-3)
+    assert r32.stats["points_ext"] > 0
+    for n in r64.assembled:
+        s = math.hypot(r64.assembled_errors[n], r32.assembled_errors[n])
+        assert abs(r64.assembled[n] - r32.assembled[n]) < 3 * s + 1e-6
+    from paper_1511_03614_gb300 import Integrator
+    prep, _ = feynman("double_box")
+    integ = Integrator(prep)
+    integ.integrate(n_iter=3, points=20000, seed=1)        # adapt the grids
+    a = integ.integrate(n_iter=1, points=20000, seed=2, precision="auto", reset_grid=False, adapt=False)
+    b = integ.integrate(n_iter=1, points=20000, seed=2, precision="auto", reset_grid=False, adapt=False,
+                        small_x=1e-2)
+    assert b.stats["units_fp32"] > a.stats["units_fp32"], (a.stats["units_fp32"], b.stats["units_fp32"])
