@@ -418,7 +418,7 @@ def run_tta(args):
     """GPU-seconds to the target relative error per eps order: plain binary64 Vegas
     against the per-unit mixed precision policy, binary32, variance-driven point
     allocation across units (*_alloc), binary64 for the points near the boundary of
-    binary32 units (*_mixed: small_x = 1e-2), the learned flow and the cubature."""
+    binary32 units (*_mixed: small_x32 = 1e-2), the learned flow and the cubature."""
     import torch
     from paper_1511_03614_gb300 import Integrator
     from paper_1511_03614_gb300.api import run_to_accuracy
@@ -438,7 +438,8 @@ def run_tta(args):
         try:
             integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
             r = run_to_accuracy(integ, target=args.target, points=pts, precision=prec, max_iters=args.max_iters,
-                                allocate=form.endswith("_alloc"), small_x=1e-2 if "_mixed" in form else 0.0)
+                                allocate=form.endswith("_alloc"),
+                                small_x32=1e-2 if "_mixed" in form else 0.0)
         except FiestaError as e:
             out["runs"][form] = {"error": str(e)}
             integ.close()

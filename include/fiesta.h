@@ -104,17 +104,20 @@ typedef struct {
                                  CUDA graph (captured on the first call, reused while the call's
                                  parameters are unchanged) */
     int32_t reserved;
-    double small_x;           /* more precision near the boundary (the paper's mixed mode, Sec. 4.6,
-                                 SmallX), where the subtraction terms cancel: > 0 promotes every
-                                 point with a coordinate below small_x one level: binary32 units
-                                 evaluate it in binary64, binary64 units in double-double (and the
-                                 FIESTA_AUTO probe counts such points as exact for binary32);
-                                 0 = off.  Units with complex results are rejected when it is set. */
+    double small_x;           /* extended precision near the boundary (the paper's mixed mode, Sec. 4.6,
+                                 SmallX), where the subtraction terms cancel: > 0 evaluates every
+                                 point of a binary64 unit with a coordinate below small_x in
+                                 double-double; 0 = off.  Units with complex results are rejected
+                                 when it is set. */
     const int64_t *unit_points;  /* nullable host array, one entry per unit of the slice: points per
                                  iteration of that unit (>= 2; <= 2^32 with Sobol), replacing
                                  points_per_iter (which still sizes the autotuner's trials).  Lets a
                                  caller spend points where the variance is (see the binding's
                                  run_to_accuracy); the point streams do not depend on it. */
+    double small_x32;         /* the same one level down: > 0 evaluates every point of a binary32
+                                 unit with a coordinate below small_x32 in binary64 (the
+                                 subtraction differences near the boundary stay binary64), and the
+                                 FIESTA_AUTO probe counts such points as exact for binary32; 0 = off. */
 } fiesta_options;
 
 typedef struct {
@@ -143,7 +146,8 @@ typedef struct {
                                  complex unit's (re, im) pair counting as one */
     int32_t threads[2];       /* block size used for binary64 [0] and binary32 [1] */
     int32_t points_per_thread[2];
-    int64_t points_ext;       /* points promoted by small_x (binary32 -> binary64, binary64 -> double-double) */
+    int64_t points_ext;       /* points promoted near the boundary (small_x: binary64 -> double-double,
+                                 small_x32: binary32 -> binary64) */
 } fiesta_stats;
 
 typedef struct fiesta_ctx fiesta_ctx;

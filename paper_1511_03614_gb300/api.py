@@ -98,7 +98,7 @@ class Integrator:
     def integrate(self, n_iter=10, points=100_000, seed=1, rng="philox", precision="fp64", adapt=True,
                   alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
                   iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
-                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0, unit_points=None):
+                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0, unit_points=None, small_x32=0.0):
         lo = min(u.order for u in self.prep.units)
         hi = max(u.order + _n_orders(u) - 1 for u in self.prep.units)
         nord = hi - lo + 1
@@ -107,7 +107,7 @@ class Integrator:
                         int(seed) & 0xFFFFFFFFFFFFFFFF, float(alpha), int(bool(skip_first)), lo, int(b), int(e),
                         int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset),
                         int(points_per_thread), int(probe_points), float(fp32_budget), int(not graph), 0,
-                        float(small_x))
+                        float(small_x), None, float(small_x32))
         if unit_points is not None:
             upts = np.ascontiguousarray(unit_points, dtype=np.int64)
             if upts.shape != (e - b,):
@@ -431,7 +431,7 @@ def allocate_points(prep, sig, n_used, values, target, floor, points, lo_frac=0.
 
 def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_iters=200, seed=1,
                     precision="fp64", rng="philox", floor=1e-2, skip_first=1, checkpoint=None, resume=None,
-                    stop_after=None, allocate=False, small_x=0.0):
+                    stop_after=None, allocate=False, small_x=0.0, small_x32=0.0):
     """Vegas until every eps order of the assembled result has sigma <= target * max(|R|, floor * max|R|).
 
     Iterations are combined per unit with inverse-variance weights across calls
@@ -444,8 +444,9 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
     seconds (the library's device time over all calls), the points, the
     iterations and the final values and errors.  ``allocate`` spends the points of
     every call after the first where the variance is (``allocate_points``) instead of
-    evenly; the total points per iteration stay nu * points.  ``small_x`` promotes
-    points near the boundary one precision level (see Integrator.integrate).
+    evenly; the total points per iteration stay nu * points.  ``small_x`` /
+    ``small_x32`` promote points near the boundary of binary64 / binary32 units one
+    precision level (see fiesta_options).
     """
     prep = integ.prep
     recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
@@ -465,7 +466,7 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
     while it < max_iters:
         r = integ.integrate(n_iter=iters_per_call, points=points, seed=seed, rng=rng, precision=precision,
                             adapt=2, reset_grid=(it == 0), iter_offset=it, assemble_result=False,
-                            unit_points=unit_pts, small_x=small_x)
+                            unit_points=unit_pts, small_x=small_x, small_x32=small_x32)
         gpu_ms += r.stats["gpu_ms"]
         points_done += r.stats["unit_points"]
         used_now = np.full(len(prep.units), float(points)) if unit_pts is None else unit_pts.astype(float)

@@ -121,14 +121,14 @@ def test_dd_rejects_complex_units():
 
 
 def test_fp32_with_binary64_near_the_boundary():
-    """small_x with the binary32 body: points near the boundary run in binary64 (the
+    """small_x32 with the binary32 body: points near the boundary run in binary64 (the
     subtraction differences there stay binary64); results within errors of binary64,
     the promoted points counted; on the double box the AUTO probe then accepts more
     units for binary32 than without promotion."""
     need_gpu()
     integ = integrator("box")
     r64 = integ.integrate(n_iter=5, points=200_000, seed=3)
-    r32 = integ.integrate(n_iter=5, points=200_000, seed=3, precision="fp32", small_x=1e-3)
+    r32 = integ.integrate(n_iter=5, points=200_000, seed=3, precision="fp32", small_x32=1e-3)
     assert r32.stats["points_ext"] > 0
     for n in r64.assembled:
         s = math.hypot(r64.assembled_errors[n], r32.assembled_errors[n])
@@ -139,5 +139,5 @@ def test_fp32_with_binary64_near_the_boundary():
     integ.integrate(n_iter=3, points=20000, seed=1)        # adapt the grids
     a = integ.integrate(n_iter=1, points=20000, seed=2, precision="auto", reset_grid=False, adapt=False)
     b = integ.integrate(n_iter=1, points=20000, seed=2, precision="auto", reset_grid=False, adapt=False,
-                        small_x=1e-2)
+                        small_x32=1e-2)
     assert b.stats["units_fp32"] > a.stats["units_fp32"], (a.stats["units_fp32"], b.stats["units_fp32"])
