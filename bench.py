@@ -450,7 +450,7 @@ def run_tta(args):
         integ.close()
     # learned proposal: flow sampling with training rounds, binary32 integrand
     from paper_1511_03614_gb300.api import run_flow
-    integ = Integrator(prep)
+    integ = Integrator(prepared(args.workload, fuse=True))       # one flow per sector, all orders
     try:
         if "flow_fp32" not in forms:
             raise _Skip()

@@ -350,11 +350,14 @@ int fiesta_sample_noalloc(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end,
  *   (set != 0) the host array `params`.
  * fiesta_flow_sample: one importance-sampling pass over units [unit_begin,
  *   unit_end): `points` points per unit from the flow (Philox stream of (seed,
- *   unit, iteration)), the integrand evaluated in `precision`; writes the per-
- *   unit mean of f/q and its variance of the mean to host arrays mean, var.
- *   The first `keep` points of each unit are kept for training.
+ *   unit, iteration)), the integrand evaluated in `precision`; writes the mean
+ *   of f/q and its variance of the mean to host arrays mean, var, one entry per
+ *   result of the slice's units (n_out per unit, in unit order).  The first
+ *   `keep` points of each unit are kept for training, with |f| (the norm of the
+ *   result vector for units with several results) as the training target.
  * fiesta_flow_train: `steps` Adam steps (learning rate lr) on the kept points,
- *   loss -sum_i w_i log q(x_i) with w_i proportional to (|f_i|/q_i)^power
+ *   loss -sum_i w_i log q(x_i) with w_i proportional to (|f_i|/q_i)^power (one
+ *   flow per unit: a fused unit's orders share it)
  *   (power 1: KL divergence, 2: variance); `loss` (nullable, host) receives the
  *   last step's loss per unit.
  * fiesta_flow_check: parity hook for one unit: the sampler at the caller's base

@@ -250,10 +250,12 @@ class Integrator:
         N.check(self.lib.fiesta_flow_params(self.ctx, int(unit), p.ctypes.data_as(C.POINTER(C.c_float)), 1))
 
     def flow_sample(self, points, seed=1, iteration=0, precision="fp32", keep=0, units=None):
-        """One pass of flow importance sampling: per-unit mean of f/q and its variance."""
+        """One pass of flow importance sampling: mean of f/q and its variance, one entry
+        per result of the units (n_out per unit, in unit order)."""
         b, e = (0, len(self.prep.units)) if units is None else units
-        m = np.empty(e - b)
-        v = np.empty(e - b)
+        nrec = sum(u.n_out for u in self.prep.units[b:e])
+        m = np.empty(nrec)
+        v = np.empty(nrec)
         st = N.Stats()
         N.check(self.lib.fiesta_flow_sample(self.ctx, b, e, int(points), int(seed), int(iteration),
                                             N.PRECISION[precision], int(keep),
@@ -542,11 +544,11 @@ def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, st
     too, with inverse-variance weights, except the first ``skip_rounds`` (default:
     half of the training rounds).  GPU seconds include the training."""
     prep = integ.prep
-    nu = len(prep.units)
+    recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
     integ.flow_init(seed=seed)
     skip = train_rounds // 2 if skip_rounds is None else skip_rounds
-    sw = np.zeros(nu)
-    swi = np.zeros(nu)
+    sw = np.zeros(len(recs))
+    swi = np.zeros(len(recs))
     gpu_ms = 0.0
     pts = 0
     res = None
@@ -566,11 +568,11 @@ def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, st
             continue
         val = swi / sw
         sig = np.sqrt(1.0 / sw)
-        values, errors = {}, {}
-        for k, u in enumerate(prep.units):
-            values[u.order] = values.get(u.order, 0.0) + val[k]
-            errors[u.order] = errors.get(u.order, 0.0) + sig[k] ** 2
-        errors = {K: math.sqrt(e) for K, e in errors.items()}
+        values, errors = _sum_parts([_record_key(prep.units[unit], o) + (val[k], sig[k])
+                                     for k, (unit, o) in enumerate(recs)])
+        if not prep.complex:
+            values = {K: z.real for K, z in values.items()}
+            errors = {K: z.real for K, z in errors.items()}
         R, E = assemble(prep, values, errors)
         big = max(abs(x) for x in R.values())
         ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)

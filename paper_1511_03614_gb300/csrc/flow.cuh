@@ -135,8 +135,9 @@ struct FlowSampleParams {
     float *tr_x;                       // [unit][keep][8]
     float *tr_lq, *tr_f;               // [unit][keep]
     const double *z_in;                // nullable: base points [points][dim] (check mode, one unit)
-    double *x_out, *lq_out, *f_out;    // nullable: per point outputs (check mode)
+    double *x_out, *lq_out, *f_out;    // nullable: per point outputs (check mode; result 0)
     double *a_out;                     // logit coordinates of x_out (check mode)
+    int out_stride;                    // records per block (largest n_out of the slice)
 };
 
 template <typename T>
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) 
     float *s_lq = reinterpret_cast<float *>(smem + off); off = align16(off + 4 * nt);
     float *s_xf = reinterpret_cast<float *>(smem + off); off = align16(off + 4 * MAXD * nt);
     float *s_af = reinterpret_cast<float *>(smem + off); off = align16(off + 4 * MAXD * nt);
+    double *s_acc = reinterpret_cast<double *>(smem + off); off = align16(off + 8 * 2 * MAXO * nt);
     double *s_red = reinterpret_cast<double *>(smem + off);
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(p.packed + unit * FLP_UNIT_BYTES);
@@ -172,7 +174,8 @@ __global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) 
 
     const int64_t per_block = (p.points + p.blocks_per_unit - 1) / p.blocks_per_unit;
     const int64_t first = blk * per_block, last = min(p.points, first + per_block);
-    double sv = 0.0, sv2 = 0.0;
+    const int no = u.n_out;
+    for (int k = 0; k < 2 * MAXO; ++k) s_acc[k * nt + tid] = 0.0;     // this thread's sums per result
     unsigned long long bad = 0;
     for (int64_t base = first; base < last; base += nt) {
         // this warp's 32 points: base + warp*32 + (0..31)
@@ -252,25 +255,34 @@ __global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) 
         const int64_t pi = wbase + lane;
         const float lqv = s_lq[tid];
         for (int j = 0; j < d; ++j) s_x[j * nt + tid] = static_cast<T>(s_xf[j * nt + tid]);
-        const T f = interpret<T>(s_code, u.n_instr, s_cons, s_slots + tid, s_x + tid, nt, u.out_slot, s_tab);
+        (void)interpret<T>(s_code, u.n_instr, s_cons, s_slots + tid, s_x + tid, nt, u.out_slot, s_tab);
         // a coordinate below the binary32 range (x = sigmoid(a) underflows; measure
         // < 1e-38 per coordinate) makes the point contribute zero
         bool in_range = true;
         for (int j = 0; j < d; ++j) in_range = in_range && s_xf[j * nt + tid] >= 1.17549435e-38f;
         if (pi < last) {
-            double v = in_range ? static_cast<double>(f) * exp(-static_cast<double>(lqv)) : 0.0;
-            if (!isfinite(v)) {
-                ++bad;
-                v = 0.0;
+            const double iq = exp(-static_cast<double>(lqv));
+            bool finite = true;
+            double f2 = 0.0;              // |f|^2 summed over the results: the training target
+            for (int k = 0; k < no; ++k) {
+                const double fk = static_cast<double>(s_slots[tid + u.outs[k] * nt]);
+                finite = finite && isfinite(in_range ? fk * iq : 0.0);
+                f2 = fma(fk, fk, f2);
             }
-            sv += v;
-            sv2 = fma(v, v, sv2);
+            if (!finite) ++bad;
+            for (int k = 0; k < no; ++k) {
+                const double v = (finite && in_range) ? static_cast<double>(s_slots[tid + u.outs[k] * nt]) * iq : 0.0;
+                s_acc[(2 * k) * nt + tid] += v;
+                s_acc[(2 * k + 1) * nt + tid] = fma(v, v, s_acc[(2 * k + 1) * nt + tid]);
+            }
+            const double f0 = static_cast<double>(s_slots[tid + u.outs[0] * nt]);
             if (pi < p.keep) {
-                // training points are kept as logit coordinates a (x may round to 1 in binary32)
+                // training points are kept as logit coordinates a (x may round to 1 in binary32);
+                // the target of a unit with several results is the norm of its result vector
                 float *dst = p.tr_x + (unit * p.keep + pi) * MAXD;
                 for (int j = 0; j < MAXD; ++j) dst[j] = j < d ? s_af[j * nt + tid] : 0.f;
                 p.tr_lq[unit * p.keep + pi] = lqv;
-                p.tr_f[unit * p.keep + pi] = static_cast<float>(f);
+                p.tr_f[unit * p.keep + pi] = static_cast<float>(no == 1 ? f0 : sqrt(f2));
             }
             if (p.x_out) {
                 for (int j = 0; j < d; ++j) {
@@ -278,18 +290,27 @@ __global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) 
                     p.a_out[pi * d + j] = s_af[j * nt + tid];
                 }
                 p.lq_out[pi] = lqv;
-                p.f_out[pi] = static_cast<double>(f);
+                p.f_out[pi] = f0;
             }
         }
         __syncwarp();
     }
-    // block sums in a fixed order -> one record per (unit, block)
-    unsigned char *red = reinterpret_cast<unsigned char *>(s_red);
-    block_sum3(sv, sv2, bad, red);
+    // block sums in a fixed order -> one record per (unit, block, result)
+    double sv[MAXO], sv2[MAXO];
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k) {
+        sv[k] = s_acc[(2 * k) * nt + tid];
+        sv2[k] = s_acc[(2 * k + 1) * nt + tid];
+    }
+    block_sum_vec<MAXO>(sv, sv2, bad, no, reinterpret_cast<unsigned char *>(s_red));
     if (tid == 0) {
         const int64_t item = (unit - p.unit_begin) * p.blocks_per_unit + blk;
-        p.part_sv[item] = sv;
-        p.part_sv2[item] = sv2;
+#pragma unroll
+        for (int k = 0; k < MAXO; ++k)
+            if (k < no) {
+                p.part_sv[item * p.out_stride + k] = sv[k];
+                p.part_sv2[item * p.out_stride + k] = sv2[k];
+            }
         p.part_bad[item] = bad;
     }
 }
@@ -649,7 +670,8 @@ size_t flow_sample_smem(int fp32, const SliceInfo &si) {
     const size_t T = fp32 ? 4 : 8;
     return align16(FLP_UNIT_BYTES) + align16(4 * si.max_instr) + align16(T * si.max_const) +
            align16(8 * LOGTAB_DOUBLES) + align16(T * MAXD * FL_THREADS) + align16(T * si.max_slots * FL_THREADS) +
-           align16(4 * FL_THREADS) + 2 * align16(4 * MAXD * FL_THREADS) + 2 * 8 * 32 + 8 * 32 + 64;
+           align16(4 * FL_THREADS) + 2 * align16(4 * MAXD * FL_THREADS) + align16(8 * 2 * MAXO * FL_THREADS) +
+           (2 * MAXO * 8 + 8) * 32 + 64;
 }
 
 int flow_launch_sample(fiesta_ctx *c, FlowSampleParams &p, int64_t nu, int fp32, const SliceInfo &si) {
@@ -724,17 +746,17 @@ int fiesta_flow_sample(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int6
         return fail(FIESTA_E_INVALID, "fiesta_flow_sample: bad unit range, point count or keep");
     if (precision != FIESTA_FP64 && precision != FIESTA_FP32)
         return fail(FIESTA_E_INVALID, "fiesta_flow_sample: precision must be FP64 or FP32");
-    for (int64_t k = unit_begin; k < unit_end; ++k)
-        if (c->units[k].n_out > 1)
-            return fail(FIESTA_E_INVALID, "fiesta_flow_sample: units with several results are not supported");
     int r = flow_alloc(c, keep);
     if (r) return r;
     FlowState *F = c->flow;
     const int64_t nu = unit_end - unit_begin;
-    const int64_t bpu = std::max<int64_t>(1, std::min<int64_t>((points + 4095) / 4096, std::max<int64_t>(1, (int64_t)c->n_sm * 4 / nu)));
-    r = ensure_buffers(c, nu * bpu, nu, 1);
-    if (r) return r;
+    // blocks of about 8192 points each: enough blocks that units of very different
+    // program length balance over the SMs (the flow and program are staged per block)
+    const int64_t bpu = std::max<int64_t>(1, (points + 8191) / 8192);
     const SliceInfo si = slice_info(c, unit_begin, unit_end);
+    const int ostride = si.max_out;
+    r = ensure_buffers(c, nu * bpu, nu, 1, ostride);
+    if (r) return r;
     FlowSampleParams p{};
     p.units = c->d_units;
     p.code = c->d_code;
@@ -757,6 +779,7 @@ int fiesta_flow_sample(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int6
     p.tr_x = F->tr_x;
     p.tr_lq = F->tr_lq;
     p.tr_f = F->tr_f;
+    p.out_stride = ostride;
     if (keep > 0) F->keep = keep;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -765,17 +788,24 @@ int fiesta_flow_sample(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int6
     CUDA_TRY(cudaMemsetAsync(c->d_unit_bad, 0, sizeof(unsigned long long) * nu, c->stream));
     r = flow_launch_sample(c, p, nu, precision == FIESTA_FP32, si);
     if (r) return r;
-    const unsigned rb = (unsigned)((nu * 32 + 255) / 256);
-    k_reduce<<<rb, 256, 0, c->stream>>>(c->d_part_sv, c->d_part_sv2, c->d_part_bad, nu, bpu, points, 1, 0,
-                                         c->d_iter_mean, c->d_iter_var, c->d_unit_bad, c->d_units, nullptr,
-                                         unit_begin, 1);
+    const unsigned rbo = (unsigned)((nu * ostride * 32 + 255) / 256);
+    k_reduce<<<rbo, 256, 0, c->stream>>>(c->d_part_sv, c->d_part_sv2, c->d_part_bad, nu, bpu, points, 1, 0,
+                                          c->d_iter_mean, c->d_iter_var, c->d_unit_bad, c->d_units, nullptr,
+                                          unit_begin, ostride);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(e1, c->stream));
     std::vector<unsigned long long> bad(nu);
-    CUDA_TRY(cudaMemcpyAsync(mean, c->d_iter_mean, sizeof(double) * nu, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(var, c->d_iter_var, sizeof(double) * nu, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> hm(nu * ostride), hv(nu * ostride);
+    CUDA_TRY(cudaMemcpyAsync(hm.data(), c->d_iter_mean, sizeof(double) * nu * ostride, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(hv.data(), c->d_iter_var, sizeof(double) * nu * ostride, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaMemcpyAsync(bad.data(), c->d_unit_bad, sizeof(unsigned long long) * nu, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    int64_t rec = 0;                       // one record per result, in unit order
+    for (int64_t k = 0; k < nu; ++k)
+        for (int o = 0; o < c->units[unit_begin + k].n_out; ++o, ++rec) {
+            mean[rec] = hm[k * ostride + o];
+            var[rec] = hv[k * ostride + o];
+        }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
@@ -897,11 +927,12 @@ int fiesta_flow_check(fiesta_ctx *c, int64_t unit, int64_t n, int32_t precision,
         if (cudaMemcpyAsync(dz, z, sizeof(double) * n * d, cudaMemcpyHostToDevice, s) != cudaSuccess)
             rc = fail(FIESTA_E_CUDA, "fiesta_flow_check: copy");
     }
-    int r = rc ? rc : ensure_buffers(c, 1, 1, 1);
+    int r = rc ? rc : ensure_buffers(c, 1, 1, 1, c->units[unit].n_out);
     if (rc == FIESTA_OK && r) rc = r;
     if (rc == FIESTA_OK) {
         const SliceInfo si = slice_info(c, unit, unit + 1);
         FlowSampleParams p{};
+        p.out_stride = c->units[unit].n_out;
         p.units = c->d_units;
         p.code = c->d_code;
         p.cons64 = c->d_cons64;

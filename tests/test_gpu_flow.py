@@ -5,6 +5,7 @@ import math
 import numpy as np
 import pytest
 
+import workloads as W
 from oracle import flow as F
 
 from gpu_common import need_gpu, feynman
@@ -97,6 +98,25 @@ def test_flow_estimates_are_unbiased_on_the_box():
     for n, v in exact.items():
         s = res["errors"][n]
         assert abs(res["values"][n] - v) < 4 * s + 1e-5, (n, res["values"][n], v, s)
+
+
+def test_flow_on_fused_units():
+    """One flow per sector for all its eps orders (trained on the norm of the result
+    vector): the box's closed form within 4 sigma, and the per-result records."""
+    need_gpu()
+    from paper_1511_03614_gb300 import Integrator, prepare_feynman
+    from paper_1511_03614_gb300.api import run_flow
+    prep = prepare_feynman(W.box(), fuse_orders=True)
+    integ = Integrator(prep)
+    integ.flow_init(seed=3)
+    m, v, st = integ.flow_sample(20_000, keep=256)
+    assert len(m) == sum(u.n_out for u in prep.units) and np.all(v > 0)
+    res = run_flow(integ, target=1e-3, points=200_000, keep=2048, train_rounds=4, steps_per_round=10,
+                   max_rounds=12)
+    exact = {-2: 2.0, -1: -math.log(2.0), 0: -2 * math.pi ** 2 / 3}
+    for n, val in exact.items():
+        s = res["errors"][n]
+        assert abs(res["values"][n] - val) < 4 * s + 1e-5, (n, res["values"][n], val, s)
 
 
 def test_flow_beats_vegas_on_a_diagonal_ridge():
