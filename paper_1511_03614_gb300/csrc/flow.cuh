@@ -27,12 +27,15 @@ constexpr int FL_L = 4, FL_HID = 64, FL_IN = 16, FL_OUT = 16;
 constexpr int FL_W1 = 0, FL_B1 = FL_W1 + FL_IN * FL_HID, FL_W2 = FL_B1 + FL_HID, FL_B2 = FL_W2 + FL_HID * FL_HID,
               FL_W3 = FL_B2 + FL_HID, FL_B3 = FL_W3 + FL_HID * FL_OUT, FL_PER_LAYER = FL_B3 + FL_OUT;
 constexpr int FL_PARAMS = FL_L * FL_PER_LAYER;                       // 25152 floats per unit
-// packed inference layout per layer: bf16 W1t[64][16], W2t[64][64], W3t[16][64]; then f32 b1, b2, b3
-constexpr int FLP_W1 = 0, FLP_W2 = FLP_W1 + FL_HID * FL_IN, FLP_W3 = FLP_W2 + FL_HID * FL_HID,
-              FLP_HALVES = FLP_W3 + FL_OUT * FL_HID;                 // 6144 bf16 per layer
+// packed inference layout per layer: bf16 W1t[64][S1], W2t[64][S2], W3t[16][S2] (transposed,
+// rows padded to S1 = 24 / S2 = 72 halves so that the eight row groups g of a B-fragment
+// load, rows g*S words apart, land in distinct shared-memory banks); then f32 b1, b2, b3
+constexpr int FLP_S1 = FL_IN + 8, FLP_S2 = FL_HID + 8;
+constexpr int FLP_W1 = 0, FLP_W2 = FLP_W1 + FL_HID * FLP_S1, FLP_W3 = FLP_W2 + FL_HID * FLP_S2,
+              FLP_HALVES = FLP_W3 + FL_OUT * FLP_S2;                 // 7296 bf16 per layer
 constexpr int FLP_BIAS = FL_HID + FL_HID + FL_OUT;                   // 144 floats per layer
-constexpr size_t FLP_LAYER_BYTES = FLP_HALVES * 2 + FLP_BIAS * 4;    // 12864
-constexpr size_t FLP_UNIT_BYTES = FLP_LAYER_BYTES * FL_L;            // 51456
+constexpr size_t FLP_LAYER_BYTES = FLP_HALVES * 2 + FLP_BIAS * 4;    // 15168
+constexpr size_t FLP_UNIT_BYTES = FLP_LAYER_BYTES * FL_L;            // 60672
 constexpr float FL_S = 4.0f;
 constexpr int FL_THREADS = 128;
 
@@ -78,7 +81,7 @@ __device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ la
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
-        const uint32_t bb0 = *reinterpret_cast<const uint32_t *>(W1t + (nt * 8 + g) * FL_IN + 2 * t);
+        const uint32_t bb0 = *reinterpret_cast<const uint32_t *>(W1t + (nt * 8 + g) * FLP_S1 + 2 * t);
         mma_bf16(c, a0, a1, 0u, 0u, bb0, 0u);
         const float bx = b1[nt * 8 + 2 * t], by = b1[nt * 8 + 2 * t + 1];
         const uint32_t r0 = pack_bf16(fmaxf(c[0] + bx, 0.f), fmaxf(c[1] + by, 0.f));
@@ -93,7 +96,7 @@ __device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ la
         float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) {
-            const __nv_bfloat16 *col = W2t + (nt * 8 + g) * FL_HID + kt * 16 + 2 * t;
+            const __nv_bfloat16 *col = W2t + (nt * 8 + g) * FLP_S2 + kt * 16 + 2 * t;
             mma_bf16(c, A[kt][0], A[kt][1], A[kt][2], A[kt][3], *reinterpret_cast<const uint32_t *>(col),
                      *reinterpret_cast<const uint32_t *>(col + 8));
         }
@@ -107,7 +110,7 @@ __device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ la
         float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) {
-            const __nv_bfloat16 *col = W3t + (nt * 8 + g) * FL_HID + kt * 16 + 2 * t;
+            const __nv_bfloat16 *col = W3t + (nt * 8 + g) * FLP_S2 + kt * 16 + 2 * t;
             mma_bf16(c, A2[kt][0], A2[kt][1], A2[kt][2], A2[kt][3], *reinterpret_cast<const uint32_t *>(col),
                      *reinterpret_cast<const uint32_t *>(col + 8));
         }
@@ -590,17 +593,17 @@ __global__ void k_flow_pack(const float *params, unsigned char *packed, int64_t 
         const float *PL = P + l * FL_PER_LAYER;
         __nv_bfloat16 *h = reinterpret_cast<__nv_bfloat16 *>(dst + l * FLP_LAYER_BYTES);
         float *b = reinterpret_cast<float *>(dst + l * FLP_LAYER_BYTES + FLP_HALVES * 2);
-        for (int e = threadIdx.x; e < FL_HID * FL_IN; e += blockDim.x) {     // W1t[n][k] = W1[k][n]
-            const int n = e / FL_IN, k = e % FL_IN;
-            h[FLP_W1 + e] = __float2bfloat16_rn(PL[FL_W1 + k * FL_HID + n]);
+        for (int e = threadIdx.x; e < FL_HID * FLP_S1; e += blockDim.x) {    // W1t[n][k] = W1[k][n]
+            const int n = e / FLP_S1, k = e % FLP_S1;
+            h[FLP_W1 + e] = __float2bfloat16_rn(k < FL_IN ? PL[FL_W1 + k * FL_HID + n] : 0.f);
         }
-        for (int e = threadIdx.x; e < FL_HID * FL_HID; e += blockDim.x) {
-            const int n = e / FL_HID, k = e % FL_HID;
-            h[FLP_W2 + e] = __float2bfloat16_rn(PL[FL_W2 + k * FL_HID + n]);
+        for (int e = threadIdx.x; e < FL_HID * FLP_S2; e += blockDim.x) {
+            const int n = e / FLP_S2, k = e % FLP_S2;
+            h[FLP_W2 + e] = __float2bfloat16_rn(k < FL_HID ? PL[FL_W2 + k * FL_HID + n] : 0.f);
         }
-        for (int e = threadIdx.x; e < FL_OUT * FL_HID; e += blockDim.x) {    // W3t[n][k] = W3[k][n]
-            const int n = e / FL_HID, k = e % FL_HID;
-            h[FLP_W3 + e] = __float2bfloat16_rn(PL[FL_W3 + k * FL_OUT + n]);
+        for (int e = threadIdx.x; e < FL_OUT * FLP_S2; e += blockDim.x) {    // W3t[n][k] = W3[k][n]
+            const int n = e / FLP_S2, k = e % FLP_S2;
+            h[FLP_W3 + e] = __float2bfloat16_rn(k < FL_HID ? PL[FL_W3 + k * FL_OUT + n] : 0.f);
         }
         for (int e = threadIdx.x; e < FLP_BIAS; e += blockDim.x)
             b[e] = e < FL_HID ? PL[FL_B1 + e] : (e < 2 * FL_HID ? PL[FL_B2 + e - FL_HID] : PL[FL_B3 + e - 2 * FL_HID]);
