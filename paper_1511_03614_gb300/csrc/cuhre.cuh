@@ -563,17 +563,15 @@ int fiesta_cuhre(fiesta_ctx *c, const fiesta_cuhre_options *opt, double *value, 
     std::vector<int32_t> passes_u(nu, 0), conv(nu, 0), hconv(nu);
     std::vector<double> htv(nu * MAXO, 0.0), hte(nu * MAXO, 0.0), tv(nu * MAXO), te(nu * MAXO);
     int bad = 0;
-    cudaEvent_t e0, e1, p0, p1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
-    CUDA_TRY(cudaEventCreate(&p0));
-    CUDA_TRY(cudaEventCreate(&p1));
-    auto destroy = [&]() {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaEventDestroy(p0);
-        cudaEventDestroy(p1);
-    };
+    struct Events {                      // destroyed on every return path
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } events;
+    for (cudaEvent_t &e : events.ev) CUDA_TRY(cudaEventCreate(&e));
+    cudaEvent_t e0 = events.ev[0], e1 = events.ev[1], p0 = events.ev[2], p1 = events.ev[3];
     CUDA_TRY(cudaEventRecord(e0, st));
     k_cuhre_init<<<(unsigned)((nu * CU_STRIDE + 255) / 256), 256, 0, st>>>(nu, S.rc[0], S.rh[0], S.runit[0]);
     CUDA_TRY(cudaMemsetAsync(S.frz_v, 0, sizeof(double) * MAXO * nu, st));
@@ -706,7 +704,6 @@ int fiesta_cuhre(fiesta_ctx *c, const fiesta_cuhre_options *opt, double *value, 
     CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    destroy();
     if (rc) return rc;
     // results
     const int lo = opt->order_lo;

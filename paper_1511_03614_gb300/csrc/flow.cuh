@@ -784,9 +784,9 @@ int fiesta_flow_sample(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int6
     p.tr_f = F->tr_f;
     p.out_stride = ostride;
     if (keep > 0) F->keep = keep;
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
+    EventPair evp;
+    if (int r0 = evp.create()) return r0;
+    cudaEvent_t e0 = evp.a, e1 = evp.b;
     CUDA_TRY(cudaEventRecord(e0, c->stream));
     CUDA_TRY(cudaMemsetAsync(c->d_unit_bad, 0, sizeof(unsigned long long) * nu, c->stream));
     r = flow_launch_sample(c, p, nu, precision == FIESTA_FP32, si);
@@ -811,8 +811,6 @@ int fiesta_flow_sample(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int6
         }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->gpu_ms = ms;
@@ -843,9 +841,13 @@ int fiesta_flow_train(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int32
         c->dfree(d_loss);
         return fail(FIESTA_E_NOMEM, "fiesta_flow_train: allocation failed");
     }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    EventPair evp;
+    if (int r0 = evp.create()) {
+        c->dfree(d_wsum);
+        c->dfree(d_loss);
+        return r0;
+    }
+    cudaEvent_t e0 = evp.a, e1 = evp.b;
     cudaEventRecord(e0, c->stream);
     int rc = FIESTA_OK;
     k_flow_wsum<<<(unsigned)nu, 128, 0, c->stream>>>(F->tr_lq, F->tr_f, F->keep, power, unit_begin, d_wsum);
@@ -891,8 +893,6 @@ int fiesta_flow_train(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int32
     }
     float ms = 0.f;
     if (rc == FIESTA_OK) cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (stats && rc == FIESTA_OK) {
         std::memset(stats, 0, sizeof(*stats));
         stats->gpu_ms = ms;
