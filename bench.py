@@ -213,7 +213,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2
     clocks = Clocks(local)
     stream = integ.stream
-    times, eval_ms, launches, eval_launches, points = [], 0.0, 0, 0, 0
+    times, eval_ms, launches, eval_iters, points = [], 0.0, 0, 0, 0
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
@@ -229,7 +229,7 @@ def run_ours(args):
         times.append(e0.elapsed_time(e1))
         eval_ms += res.stats["eval_ms"]
         launches += res.stats["kernels_launched"]
-        eval_launches += res.stats["eval_launches"]
+        eval_iters += iters             # one evaluation pass (all its launches) per iteration
         points += res.stats["unit_points"]          # evaluations of (sector, order) integrands
     torch.cuda.synchronize()
     barrier(world)
@@ -239,12 +239,13 @@ def run_ours(args):
     all_points = sum_over_ranks(points, world)
     value = all_points / (t_max * 1e-3)
 
-    # roofline of the evaluation kernel (dominant): algorithmic work per launch
+    # roofline of the evaluation kernel (dominant): algorithmic work per evaluation pass (one
+    # launch per iteration, or one per slot-size class when programs differ widely in size)
     costs = op_costs(peaks)
     per_unit = [unit_work(u.program, costs, u.dim, True) for u in prep.units]
     flops_per_launch = sum(f for f, _ in per_unit) * pts
     slots_per_launch = sum(s for _, s in per_unit) * pts
-    avg_eval_s = eval_ms / max(eval_launches, 1) * 1e-3
+    avg_eval_s = eval_ms / max(eval_iters, 1) * 1e-3     # the evaluation kernel's time per iteration
     achieved = 2.0 * slots_per_launch / avg_eval_s * 1e-12          # FMA-equivalent TFLOP/s
     peak_meas = peaks[0]
     nominal = 1.25
@@ -256,11 +257,12 @@ def run_ours(args):
                 "frac": achieved / peak_meas, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_eval<double, Philox, 6> "
                                   "on the fused box (12 units x 2e5 points, one launch)" if traffic else None,
-                "kernel": "k_eval", "work": "FMA-equivalent pipe slots x 2 per launch (log/div weighted by "
+                "kernel": "k_eval", "work": "FMA-equivalent pipe slots x 2 per evaluation pass (log/div weighted by "
                 "measured cost)", "peak_source": "measured in-process (fiesta_probe_peaks)",
                 "nominal_fp64_tflops": nominal,
                 "algorithmic_tflops": flops_per_launch / avg_eval_s * 1e-12,
-                "eval_ms_per_launch": avg_eval_s * 1e3,
+                "eval_ms_per_pass": avg_eval_s * 1e3,
+                "eval_launches_per_pass": res.stats["eval_launches"] // max(iters, 1) if res else None,
                 "peaks_measured": {"fp64_tflops": peaks[0], "fp64_log_cuda_gps": peaks[1], "fp64_div_gps": peaks[2],
                                    "fp32_tflops": peaks[3], "fp32_log_gps": peaks[4], "fp32_div_gps": peaks[5],
                                    "fp64_log_table_gps": peaks[6], "fp64_atan2_gps": peaks[7]},
