@@ -42,14 +42,22 @@ def shard_slices(units, world):
 
 
 def combine_shards(per_rank_units, orders):
-    """Per order: sum of unit values, sqrt of the sum of squared errors (Sec. 4.3)."""
-    val = {K: 0.0 for K in orders}
-    err = {K: 0.0 for K in orders}
+    """Per order: sum of unit values, sqrt of the sum of squared errors (Sec. 4.3).
+    Records of complex units (``part`` 1: imaginary) give complex values, with errors
+    complex(sigma_re, sigma_im)."""
+    val = {K: [0.0, 0.0] for K in orders}
+    err = {K: [0.0, 0.0] for K in orders}
+    cplx = False
     for units in per_rank_units:
         for u in units:
-            val[u["order"]] += u["value"]
-            err[u["order"]] += u["sigma"] ** 2
-    return val, {K: math.sqrt(e) for K, e in err.items()}
+            p = u.get("part", 0)
+            cplx = cplx or p == 1
+            val[u["order"]][p] += u["value"]
+            err[u["order"]][p] += u["sigma"] ** 2
+    if cplx:
+        return ({K: complex(*v) for K, v in val.items()},
+                {K: complex(math.sqrt(e[0]), math.sqrt(e[1])) for K, e in err.items()})
+    return {K: v[0] for K, v in val.items()}, {K: math.sqrt(e[0]) for K, e in err.items()}
 
 
 def combine_replicas(per_rank_units):

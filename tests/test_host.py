@@ -167,3 +167,35 @@ def test_complex_programs_match_oracle(fuse):
             a = Fv[:, 2 * k] + 1j * Fv[:, 2 * k + 1]
             assert np.all(np.abs(a - b) <= 1e-12 * np.maximum(P.magnitude_numpy(o, X), np.abs(b))), (u.sector, k)
 
+
+
+def test_combine_shards_complex_records():
+    """Sharded per-unit records of complex units sum re and im separately."""
+    from paper_1511_03614_gb300.shard import combine_shards
+    r0 = [dict(order=-1, part=0, value=1.0, sigma=0.3), dict(order=-1, part=1, value=2.0, sigma=0.4)]
+    r1 = [dict(order=-1, part=0, value=0.5, sigma=0.4), dict(order=-1, part=1, value=-1.0, sigma=0.3)]
+    v, e = combine_shards([r0, r1], (-1,))
+    assert v[-1] == complex(1.5, 1.0) and abs(e[-1] - complex(0.5, 0.5)) < 1e-15
+    v, e = combine_shards([[dict(order=0, value=1.0, sigma=0.6)], [dict(order=0, value=2.0, sigma=0.8)]], (0,))
+    assert v[0] == 3.0 and abs(e[0] - 1.0) < 1e-15
+
+
+def test_allocate_points_neyman():
+    """Neyman allocation: with equal spreads the points go as 1/sqrt(cost); a unit
+    with four times the variance gets twice the points; the total cost is that of the
+    uniform allocation (before clamping)."""
+    import numpy as np
+    from paper_1511_03614_gb300.api import allocate_points
+    prep = prepare_feynman(W.box())
+    nu = len(prep.units)
+    values = {-2: 2.0, -1: -0.69, 0: -6.58}
+    sig = np.full(nu, 1e-3)
+    n_used = np.full(nu, 1e6)
+    N = allocate_points(prep, sig, n_used, values, 1e-4, 1e-2, 100_000, lo_frac=0.0, hi_mult=1e9)
+    cost = np.array([len(u.program.code) + 4 * u.dim + 8 for u in prep.units], dtype=float)
+    assert abs(np.sum(N * cost) / (100_000 * cost.sum()) - 1) < 1e-3
+    sig2 = sig.copy()
+    sig2[3] *= 2.0
+    N2 = allocate_points(prep, sig2, n_used, values, 1e-4, 1e-2, 100_000, lo_frac=0.0, hi_mult=1e9)
+    ratio = (N2[3] / N2[4]) / (N[3] / N[4])
+    assert abs(ratio - 2.0) < 0.01, ratio
