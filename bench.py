@@ -420,7 +420,8 @@ def run_tta(args):
     """GPU-seconds to the target relative error per eps order: plain binary64 Vegas
     against the per-unit mixed precision policy, binary32, variance-driven point
     allocation across units (*_alloc), binary64 for the points near the boundary of
-    binary32 units (*_mixed: small_x32 = 1e-2), the learned flow and the cubature."""
+    binary32 units (*_mixed: small_x32 = 1e-2), randomised quasi-Monte Carlo on the adapted
+    grids (rqmc_*), the learned flow and the cubature."""
     import torch
     from paper_1511_03614_gb300 import Integrator
     from paper_1511_03614_gb300.api import run_to_accuracy
@@ -466,6 +467,23 @@ def run_tta(args):
     except _Skip:
         pass
     integ.close()
+    # randomised quasi-Monte Carlo on adapted Vegas grids (Sobol replicates), fused units
+    from paper_1511_03614_gb300.api import run_to_accuracy_rqmc
+    for form in ("rqmc_fp64", "rqmc_fp32"):
+        if form not in forms:
+            continue
+        integ = Integrator(prepared(args.workload, fuse=True))
+        try:
+            prec = form.split("_")[1]
+            integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
+            r = run_to_accuracy_rqmc(integ, target=args.target, points=1 << 18, precision=prec)
+            out["runs"][form] = {"gpu_s": r["gpu_s"], "points": r["points"], "rounds": r["rounds"],
+                                 "points_per_replicate": r["points_per_replicate"], "converged": r["converged"],
+                                 "values": {str(n): [_num(r["values"][n]), _num(r["errors"][n])]
+                                            for n in r["values"]}}
+        except FiestaError as e:
+            out["runs"][form] = {"error": str(e)}
+        integ.close()
     # deterministic cubature (Genz-Malik rule, binary64), its error bound against the target
     from paper_1511_03614_gb300.api import run_cuhre_to_accuracy
     integ = Integrator(prepared(args.workload, fuse=True))

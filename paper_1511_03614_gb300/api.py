@@ -536,6 +536,65 @@ def run_cuhre_to_accuracy(integ, target=1e-4, floor=1e-2, rel_tol=None, shrink=0
     return res
 
 
+def run_to_accuracy_rqmc(integ, target=1e-4, points=1 << 18, replicates=8, adapt_iters=6, adapt_points=None,
+                         max_rounds=12, seed=1, precision="fp64", floor=1e-2, max_points=1 << 30):
+    """Randomised quasi-Monte Carlo on Vegas grids.  The grids are first adapted with
+    ``adapt_iters`` Philox iterations; then each round integrates every unit with
+    ``replicates`` independent digital shifts of a Sobol sequence of N points on the
+    frozen grids (one iteration each, no adaptation).  The replicate means are
+    independent unbiased estimates, so a unit's estimate is their average and its
+    error their standard deviation over sqrt(replicates) (no variance formula for
+    correlated points is needed).  N doubles every round (Sobol points come in powers
+    of two) until every eps order meets the target (the rule of run_to_accuracy);
+    rounds are combined with inverse-variance weights.  Returns what run_to_accuracy
+    returns, with ``rounds`` and ``points_per_replicate``."""
+    prep = integ.prep
+    recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
+    gpu_ms, pts = 0.0, 0
+    r = integ.integrate(n_iter=adapt_iters, points=adapt_points or points, seed=seed, rng="philox",
+                        precision=precision, adapt=2, reset_grid=True, assemble_result=False)
+    gpu_ms += r.stats["gpu_ms"]
+    pts += r.stats["unit_points"]
+    sw = np.zeros(len(recs))
+    swi = np.zeros(len(recs))
+    n = int(points)
+    res = None
+    for rnd in range(max_rounds):
+        r = integ.integrate(n_iter=replicates, points=n, seed=seed + 1 + rnd, rng="sobol", precision=precision,
+                            adapt=False, reset_grid=False, iter_offset=1000 + rnd * replicates,
+                            assemble_result=False)
+        gpu_ms += r.stats["gpu_ms"]
+        pts += r.stats["unit_points"]
+        for k, (unit, o) in enumerate(recs):
+            m, _ = integ.iterations(unit, replicates, o)
+            mu = float(np.mean(m))
+            var = float(np.var(m, ddof=1)) / replicates if replicates > 1 else 0.0
+            w = 1.0 / var if var > 0 else 1e300
+            sw[k] += w
+            swi[k] += w * mu
+        val = swi / sw
+        sig = np.sqrt(1.0 / sw)
+        if prep.complex:
+            values, errors = _sum_parts([_record_key(prep.units[unit], o) + (val[k], sig[k])
+                                         for k, (unit, o) in enumerate(recs)])
+        else:
+            values, errors = {}, {}
+            for k, (unit, o) in enumerate(recs):
+                K = prep.units[unit].order + o
+                values[K] = values.get(K, 0.0) + val[k]
+                errors[K] = errors.get(K, 0.0) + sig[k] ** 2
+            errors = {K: math.sqrt(e) for K, e in errors.items()}
+        R, E = assemble(prep, values, errors)
+        big = max(abs(v) for v in R.values())
+        ok = all(abs(E[n_]) <= target * max(abs(R[n_]), floor * big) for n_ in R)
+        res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=rnd + 1, points_per_replicate=n, values=R, errors=E,
+                   converged=ok, unit_values=val.copy(), unit_sigmas=sig.copy())
+        if ok or 2 * n > max_points:
+            break
+        n *= 2
+    return res
+
+
 def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, steps_per_round=20, lr=2e-3,
              power=1, max_rounds=200, seed=1, precision="fp32", floor=1e-2, skip_rounds=None):
     """Learned proposal: per unit, alternate flow sampling (an unbiased estimate each
