@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fuse", type=int, default=1, help="1: one unit per sector carrying all its eps orders")
-    ap.add_argument("--forms", default="fp64,auto,fp32,fp64_alloc,auto_alloc,flow_fp32,cuhre_fp64",
+    ap.add_argument("--forms", default="fp64,auto,fp32,fp64_alloc,auto_alloc,rqmc_fp64,flow_fp32,cuhre_fp64",
                     help="tta mode: comma-separated forms to run")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
@@ -469,14 +469,14 @@ def run_tta(args):
     integ.close()
     # randomised quasi-Monte Carlo on adapted Vegas grids (Sobol replicates), fused units
     from paper_1511_03614_gb300.api import run_to_accuracy_rqmc
-    for form in ("rqmc_fp64", "rqmc_fp32"):
+    for form in ("rqmc_fp64",):
         if form not in forms:
             continue
         integ = Integrator(prepared(args.workload, fuse=True))
         try:
             prec = form.split("_")[1]
             integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
-            r = run_to_accuracy_rqmc(integ, target=args.target, points=1 << 18, precision=prec)
+            r = run_to_accuracy_rqmc(integ, target=args.target, points=1 << 18, precision=prec, max_points=1 << 22)
             out["runs"][form] = {"gpu_s": r["gpu_s"], "points": r["points"], "rounds": r["rounds"],
                                  "points_per_replicate": r["points_per_replicate"], "converged": r["converged"],
                                  "values": {str(n): [_num(r["values"][n]), _num(r["errors"][n])]

@@ -537,7 +537,7 @@ def run_cuhre_to_accuracy(integ, target=1e-4, floor=1e-2, rel_tol=None, shrink=0
 
 
 def run_to_accuracy_rqmc(integ, target=1e-4, points=1 << 18, replicates=8, adapt_iters=6, adapt_points=None,
-                         max_rounds=12, seed=1, precision="fp64", floor=1e-2, max_points=1 << 30):
+                         max_rounds=12, seed=1, precision="fp64", floor=1e-2, max_points=1 << 24):
     """Randomised quasi-Monte Carlo on Vegas grids.  The grids are first adapted with
     ``adapt_iters`` Philox iterations; then each round integrates every unit with
     ``replicates`` independent digital shifts of a Sobol sequence of N points on the
@@ -546,8 +546,11 @@ def run_to_accuracy_rqmc(integ, target=1e-4, points=1 << 18, replicates=8, adapt
     error their standard deviation over sqrt(replicates) (no variance formula for
     correlated points is needed).  N doubles every round (Sobol points come in powers
     of two) until every eps order meets the target (the rule of run_to_accuracy);
-    rounds are combined with inverse-variance weights.  Returns what run_to_accuracy
-    returns, with ``rounds`` and ``points_per_replicate``."""
+    rounds are combined with inverse-variance weights; the sequence stops growing at
+    ``max_points`` per replicate.  Binary64 is the intended precision: binary32
+    rounding near the boundary adds point-wise noise that the replicate spread does
+    not average like the quadrature error.  Returns what run_to_accuracy returns, with
+    ``rounds`` and ``points_per_replicate``."""
     prep = integ.prep
     recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
     gpu_ms, pts = 0.0, 0
