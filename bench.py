@@ -9,8 +9,13 @@ refinement and the per-order assembly.  By default each sector is one fused
 unit that evaluates all its orders at every point (--fuse 0: one unit per
 sector and order); the metric counts evaluations of (sector, order) integrands.
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the oracle (the
-plain CPU restatement of the method) on a bounded sample of the same workload.
+Prints one JSON line (rank 0).  After the timed region the line also carries
+``time_to_1e-4``: GPU-seconds to 1e-4 relative error on every order, plain
+binary64 Vegas against randomised QMC, AUTO precision with allocation and the
+cubature, measured live (--no-tta skips it).  ``--mode tta`` runs the same
+comparison with more forms on any workload, ``--mode cuhre`` the cubature's
+evaluation rate.  ``--impl reference`` times the oracle (the plain CPU
+restatement of the method) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -49,6 +54,7 @@ def parse():
     ap.add_argument("--iters", type=int, default=0, help="Vegas iterations per step (0: workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tta", action="store_true", help="skip the live time-to-1e-4 comparison")
     ap.add_argument("--fuse", type=int, default=1, help="1: one unit per sector carrying all its eps orders")
     ap.add_argument("--forms", default="fp64,auto,fp32,fp64_alloc,auto_alloc,rqmc_fp64,flow_fp32,cuhre_fp64",
                     help="tta mode: comma-separated forms to run")
@@ -294,6 +300,13 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(prep, args.workload, 12.0)
 
+    # the metric's second part, measured live on the same GPU after the timed region:
+    # GPU-seconds to 1e-4 relative error on every eps order, plain binary64 Vegas against
+    # the faster forms (randomised QMC, per-unit binary32 with allocation, cubature)
+    tta = None
+    if rank == 0 and world == 1 and not args.no_tta and args.workload in ("box", "bubble", "box_physical"):
+        tta = time_to_accuracy(args.workload, 1e-4)
+
     if rank == 0:
         line = {
             "metric": "sampling points/s", "value": value, "unit": "points/s", "n_gpus": world,
@@ -326,11 +339,40 @@ def run_ours(args):
             "clocks": ck,
             "results": {str(n): [_num(res.assembled[n]), _num(res.assembled_errors[n])] for n in res.assembled}
             if res and res.assembled else None,
+            "time_to_1e-4": tta,
         }
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def time_to_accuracy(workload, target):
+    """GPU-seconds (the library's device time) to `target` relative error on every eps
+    order: plain binary64 Vegas (one unit per sector and order) against randomised QMC
+    on the adapted grids, AUTO precision with point allocation, and the cubature (both
+    on fused units).  Errors are reported, not raised: this is an addition to the line."""
+    from paper_1511_03614_gb300 import Integrator
+    from paper_1511_03614_gb300.api import run_to_accuracy, run_to_accuracy_rqmc, run_cuhre_to_accuracy
+    out = {"target": target, "unit": "GPU-s", "workload": workload}
+    runs = (("fp64_vegas", False, lambda ig: run_to_accuracy(ig, target=target, points=1_000_000, max_iters=200)),
+            ("rqmc_fp64", True, lambda ig: run_to_accuracy_rqmc(ig, target=target, points=1 << 18,
+                                                                max_points=1 << 22)),
+            ("auto_alloc", False, lambda ig: run_to_accuracy(ig, target=target, points=1_000_000, max_iters=200,
+                                                             precision="auto", allocate=True)),
+            ("cuhre_fp64", True, lambda ig: run_cuhre_to_accuracy(ig, target=target)))
+    for name, fuse, fn in runs:
+        try:
+            ig = Integrator(prepared(workload, fuse=fuse))
+            r = fn(ig)
+            out[name] = {"gpu_s": r["gpu_s"], "converged": r["converged"]}
+            ig.close()
+        except Exception as e:          # noqa: BLE001 - reported in the line instead
+            out[name] = {"error": str(e)[:200]}
+    base = out.get("fp64_vegas", {}).get("gpu_s")
+    out["speedup_vs_fp64_vegas"] = {k: base / v["gpu_s"] for k, v in out.items()
+                                    if isinstance(v, dict) and v.get("gpu_s") and base and k != "fp64_vegas"}
+    return out
 
 
 def _oracle_lam(workload):
