@@ -45,6 +45,19 @@ def _sum_parts(records):
             {K: complex(math.sqrt(x[0]), math.sqrt(x[1])) for K, x in e.items()})
 
 
+def _assembled(prep, recs, val, sig):
+    """Per-order sums of (unit, result) records with values ``val`` and standard errors
+    ``sig`` (mean-square combination, Sec. 4.3), then the prefactor series: complex
+    values for a problem with complex units.  Returns (assembled, errors, per-order sums)."""
+    values, errors = _sum_parts([_record_key(prep.units[unit], o) + (val[k], sig[k])
+                                 for k, (unit, o) in enumerate(recs)])
+    if not prep.complex:
+        values = {K: z.real for K, z in values.items()}
+        errors = {K: z.real for K, z in errors.items()}
+    R, E = assemble(prep, values, errors)
+    return R, E, values
+
+
 class Integrator:
     """Holds the device copy of a Prepared set of units (one fiesta_ctx)."""
 
@@ -489,17 +502,7 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
             continue
         val = swi / sw
         sig = np.sqrt(1.0 / sw)
-        if prep.complex:
-            values, errors = _sum_parts([_record_key(prep.units[unit], o) + (val[k], sig[k])
-                                         for k, (unit, o) in enumerate(recs)])
-        else:
-            values, errors = {}, {}
-            for k, (unit, o) in enumerate(recs):
-                K = prep.units[unit].order + o
-                values[K] = values.get(K, 0.0) + val[k]
-                errors[K] = errors.get(K, 0.0) + sig[k] ** 2
-            errors = {K: math.sqrt(e) for K, e in errors.items()}
-        R, E = assemble(prep, values, errors)
+        R, E, values = _assembled(prep, recs, val, sig)
         big = max(abs(v) for v in R.values())
         ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)
         res = dict(gpu_s=gpu_ms * 1e-3, points=points_done, iterations=it, values=R, errors=E, converged=ok,
@@ -577,17 +580,7 @@ def run_to_accuracy_rqmc(integ, target=1e-4, points=1 << 18, replicates=8, adapt
             swi[k] += w * mu
         val = swi / sw
         sig = np.sqrt(1.0 / sw)
-        if prep.complex:
-            values, errors = _sum_parts([_record_key(prep.units[unit], o) + (val[k], sig[k])
-                                         for k, (unit, o) in enumerate(recs)])
-        else:
-            values, errors = {}, {}
-            for k, (unit, o) in enumerate(recs):
-                K = prep.units[unit].order + o
-                values[K] = values.get(K, 0.0) + val[k]
-                errors[K] = errors.get(K, 0.0) + sig[k] ** 2
-            errors = {K: math.sqrt(e) for K, e in errors.items()}
-        R, E = assemble(prep, values, errors)
+        R, E, values = _assembled(prep, recs, val, sig)
         big = max(abs(v) for v in R.values())
         ok = all(abs(E[n_]) <= target * max(abs(R[n_]), floor * big) for n_ in R)
         res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=rnd + 1, points_per_replicate=n, values=R, errors=E,
@@ -630,12 +623,7 @@ def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, st
             continue
         val = swi / sw
         sig = np.sqrt(1.0 / sw)
-        values, errors = _sum_parts([_record_key(prep.units[unit], o) + (val[k], sig[k])
-                                     for k, (unit, o) in enumerate(recs)])
-        if not prep.complex:
-            values = {K: z.real for K, z in values.items()}
-            errors = {K: z.real for K, z in errors.items()}
-        R, E = assemble(prep, values, errors)
+        R, E, values = _assembled(prep, recs, val, sig)
         big = max(abs(x) for x in R.values())
         ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)
         res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=r + 1, values=R, errors=E, converged=ok,
