@@ -199,3 +199,13 @@ def test_allocate_points_neyman():
     N2 = allocate_points(prep, sig2, n_used, values, 1e-4, 1e-2, 100_000, lo_frac=0.0, hi_mult=1e9)
     ratio = (N2[3] / N2[4]) / (N[3] / N[4])
     assert abs(ratio - 2.0) < 0.01, ratio
+
+
+def test_no_cpu_fallback():
+    """Without a GPU the product path refuses to run (no silent CPU fallback)."""
+    import torch
+    from paper_1511_03614_gb300 import Integrator
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError, match="CUDA"):
+        Integrator(prepare_feynman(W.bubble()))
