@@ -65,12 +65,12 @@ def parse():
     return ap.parse_args()
 
 
-def prepared(workload, fuse=False):
+def prepared(workload, fuse=False, mix=1):
     import workloads as W
     from paper_1511_03614_gb300 import prepare_feynman, prepare_direct
     if workload == "stress":
         return prepare_direct(W.stress_suite(), "stress")
-    return prepare_feynman(getattr(W, workload)(), fuse_orders=bool(fuse))
+    return prepare_feynman(getattr(W, workload)(), fuse_orders=bool(fuse), mix_sectors=mix)
 
 
 def dist_setup(args):
@@ -511,10 +511,11 @@ def run_tta(args):
     integ.close()
     # randomised quasi-Monte Carlo on adapted Vegas grids (Sobol replicates), fused units
     from paper_1511_03614_gb300.api import run_to_accuracy_rqmc
-    for form in ("rqmc_fp64",):
+    for form in ("rqmc_fp64", "rqmc_fp64_mix4"):
         if form not in forms:
             continue
-        integ = Integrator(prepared(args.workload, fuse=True))
+        # *_mix4: four sectors of equal dimension summed into one program (MixSectors)
+        integ = Integrator(prepared(args.workload, fuse=True, mix=4 if form.endswith("mix4") else 1))
         try:
             prec = form.split("_")[1]
             integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning

@@ -233,6 +233,28 @@ def sector_graph(sec, orders):
     return g, outs
 
 
+def mixed_graph(secs, orders):
+    """(Graph, result nodes) summing the integrands of several sectors of the same
+    dimension over the common unit cube, every order in ``orders`` (the paper's
+    MixSectors option, Sec. 4.4: fewer, longer integrands; the integral of the sum is
+    the sum of the sector integrals).  Sector j's variables are the coordinates
+    x_0..x_{d-1} in its own order; an order below a sector's lowest contributes 0."""
+    dims = {len(s.variables) for s in secs}
+    if len(dims) != 1:
+        raise ValueError("mixed sectors must have one dimension")
+    g = Graph()
+    evs = [_SectorEval(g, s) for s in secs]
+    outs = []
+    for K in orders:
+        nodes = [ev.unit(K) for ev in evs if K >= -len(ev.S)]
+        nodes = [n for n in nodes if n is not None]
+        acc = g.c(0.0) if not nodes else nodes[0]
+        for n in nodes[1:]:
+            acc = g.add(acc, n)
+        outs.append(acc)
+    return g, outs
+
+
 # ---------------------------------------------------------------------------
 # Physical kinematics: contour deformation
 # ---------------------------------------------------------------------------

@@ -28,6 +28,7 @@ class Unit:
     n_out: int = 1            # results: orders order .. order + n_out - 1 (fused multi-order unit)
     cplx: bool = False        # deformed contour: results are (re, im) pairs, orders order .. order + n_out/2 - 1
     lam: float = None         # the deformation parameter of a complex unit
+    sectors: tuple = None     # mixed units: the sectors whose integrands the program sums
 
 
 @dataclasses.dataclass
@@ -93,7 +94,44 @@ def _sector_lambda(sec, lam, lam_max):
     return I.choose_lambda(sec, lam_max)
 
 
-def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=1.0):
+def _mix_units(secs, real, Ks_of, group, max_slots=72):
+    """Mixed units (the paper's MixSectors): consecutive real sectors of equal
+    dimension, up to ``group`` at a time, as one program summing their fused
+    integrands.  A group also closes when its program would need more than
+    ``max_slots`` slots (the slot file lives in shared memory, per thread)."""
+
+    def build(run):
+        lo = min(Ks_of(secs[i])[0] for i in run)
+        hi = max(Ks_of(secs[i])[-1] for i in run)
+        Ks = list(range(lo, hi + 1))
+        if len(Ks) > MAX_OUT:
+            return None
+        g, outs = I.mixed_graph([secs[i] for i in run], Ks)
+        d = len(secs[run[0]].variables)
+        prog = B.emit(g, outs, d)
+        if len(run) > 1 and prog.n_slots > max_slots:
+            return None
+        return Unit(run[0], Ks[0], d, prog, 0, n_out=len(Ks), sectors=tuple(run))
+
+    units, run, best = [], [], None
+    for i in real:
+        if not Ks_of(secs[i]):
+            continue
+        if run and (len(run) == group or len(secs[i].variables) != len(secs[run[0]].variables)):
+            units.append(best)
+            run, best = [], None
+        trial = build(run + [i])
+        if trial is None:                  # the group is full: start a new one with i
+            units.append(best)
+            run, best = [i], build([i])
+        else:
+            run, best = run + [i], trial
+    if best is not None:
+        units.append(best)
+    return units
+
+
+def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=1.0, mix_sectors=1):
     """Units of a Feynman integral; with ``fuse_orders`` one unit per sector carries all
     its eps orders (a vector-valued integrand with one Vegas grid).
 
@@ -102,6 +140,8 @@ def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=
     results; ``lam`` fixes the deformation parameter (a number, or a callable of the
     sector), else it is chosen per sector by ``integrand.choose_lambda`` up to lam_max.
     A sector where no parameter keeps Im F <= 0 raises ValueError.
+    ``mix_sectors`` > 1 sums that many consecutive real sectors of equal dimension into
+    one program with all their orders (the paper's MixSectors; implies fused orders).
     """
     U, F = symanzik(problem)
     n = len(problem.propagators)
@@ -111,16 +151,20 @@ def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=
     q0, _ = PF.series(problem.indices, L, 0)
     khi = problem.order + q0
     units, lams = [], []
+    Ks_of = lambda s: list(range(max(kmin, I.min_order(s)), khi + 1))
     for si, sec in enumerate(secs):
-        Ks = list(range(max(kmin, I.min_order(sec)), khi + 1))
+        Ks = Ks_of(sec)
         lm = _sector_lambda(sec, lam, lam_max)
         lams.append(lm)
         if not Ks:
             continue
         if lm is None:
-            units += _real_units(si, sec, Ks, fuse_orders)
+            if mix_sectors <= 1:
+                units += _real_units(si, sec, Ks, fuse_orders)
         else:
             units += _complex_units(si, sec, Ks, fuse_orders, lm)
+    if mix_sectors > 1:
+        units = _mix_units(secs, [i for i, l in enumerate(lams) if l is None], Ks_of, mix_sectors) + units
     for k, u in enumerate(units):
         u.rng_key = k
     pre = PF.series(problem.indices, L, problem.order - kmin)

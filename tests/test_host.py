@@ -209,3 +209,31 @@ def test_no_cpu_fallback():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError, match="CUDA"):
         Integrator(prepare_feynman(W.bubble()))
+
+
+@pytest.mark.parametrize("name,group", [("box", 3), ("double_box", 4)])
+def test_mixed_sector_programs_match_oracle_sums(name, group):
+    """MixSectors: every sector lands in exactly one mixed unit, and each result of a
+    mixed program is the sum over its sectors of the oracle's integrands of that order."""
+    prob = getattr(W, name)()
+    prep = prepare_feynman(prob, mix_sectors=group)
+    orc = P.feynman_problem(prob)
+    cover = sorted(i for u in prep.units for i in u.sectors)
+    assert cover == list(range(len(prep.sectors)))
+    by = {(u.sector, u.order): u for u in orc.units}
+    rng = np.random.default_rng(8)
+    idx = range(len(prep.units)) if len(prep.units) < 12 else rng.choice(len(prep.units), 10, replace=False)
+    for i in idx:
+        u = prep.units[i]
+        X = rng.uniform(0.05, 0.95, size=(16, u.dim))
+        Fv = run(u.program, X)
+        Fv = Fv[:, None] if Fv.ndim == 1 else Fv
+        for k in range(u.n_out):
+            ref = np.zeros(len(X))
+            mag = np.zeros(len(X))
+            for s in u.sectors:
+                o = by.get((s, u.order + k))
+                if o is not None:
+                    ref += o.f_numpy(X)
+                    mag += P.magnitude_numpy(o, X)
+            assert np.all(np.abs(Fv[:, k] - ref) <= 1e-12 * np.maximum(mag, 1e-300)), (i, k)
