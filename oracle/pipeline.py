@@ -136,12 +136,18 @@ def assemble(prob, val, err):
 
 
 def _absify(e):
-    """Sum of absolute values of the additive terms at every level of the expression.
+    """Condition-scaled magnitude M of an expression (the per-point tolerance scale).
 
-    |f_computed - f| <= c u M(x) bounds the rounding error of any evaluation
-    order of f (u the unit roundoff, c of the order of the operation count);
-    M is the condition-scaled magnitude used for per-point tolerances where the
-    subtraction differences cancel.
+    Sums: the sum of the magnitudes of the terms; products: the product of the
+    magnitudes of the factors; a power b^x: |b|^x (1 + |x| (M(b)/|b| - 1)); a
+    logarithm log b: |log b| + M(b)/|b|; numbers and variables: their absolute
+    value.  This is first-order forward error propagation: a relative error
+    r = c u M(b)/|b| of b becomes |x| r in b^x and an absolute error r in log b,
+    so |f_computed - f| <= c u M(x) bounds the rounding error of any evaluation
+    order of f (u the unit roundoff, c of the order of the expression depth),
+    and M >= |f| everywhere.  Where no base cancels (M(b) = |b|) a power adds
+    nothing and a logarithm adds 1.  M is what the per-point tolerances scale
+    with where the pole-subtraction differences cancel.
     """
     if e.is_Add:
         return sp.Add(*[_absify(a) for a in e.args])
@@ -149,11 +155,14 @@ def _absify(e):
         return sp.Mul(*[_absify(a) for a in e.args])
     if e.is_Pow:
         b, x = e.args
-        return sp.Pow(_absify(b), x)
+        mb, ab = _absify(b), sp.Abs(b)
+        if mb == ab:
+            return sp.Pow(ab, x)
+        return sp.Pow(ab, x) * (1 + sp.Abs(x) * (mb / ab - 1))
     if isinstance(e, sp.log):
-        return sp.Abs(e) + 1
-    if e.is_Number:
-        return sp.Abs(e)
+        b = e.args[0]
+        mb, ab = _absify(b), sp.Abs(b)
+        return sp.Abs(e) + (1 if mb == ab else mb / ab)
     return sp.Abs(e)
 
 

@@ -370,3 +370,68 @@ def test_rqmc_digital_shift_replicates():
     assert covered >= 32, covered
     mc_sigma = np.std(f(np.random.default_rng(0).uniform(size=(100000, 2)))) / math.sqrt(8 * 4096)
     assert np.mean(errs) < 0.05 * mc_sigma
+
+
+# ------------------------------------------- condition-scaled magnitude M(x)
+# M sets the per-point tolerance of every parity test where the pole-subtraction
+# differences cancel (|f_gpu - f| <= c u M), so it is pinned to closed forms: an M
+# that is too large would silently loosen those tests, one that is too small would
+# fail them spuriously.
+
+def _magnitude(expr, X):
+    syms = sorted(expr.free_symbols, key=lambda s: int(s.name[1:]))
+    unit = P.Unit(0, 0, tuple(int(s.name[1:]) for s in syms), expr)
+    return P.magnitude_numpy(unit, np.atleast_2d(X))
+
+
+def test_magnitude_closed_forms():
+    t1, t2 = S.tsym(1), S.tsym(2)
+    X2 = np.array([[0.3, 0.2], [0.7, 0.05], [0.5, 0.5 - 2.0 ** -20]])      # t1 > t2
+    X1 = np.array([[0.3], [2.0 ** -20], [0.9]])
+    a, b = X2[:, 0], X2[:, 1]
+    x = X1[:, 0]
+    L = np.log(a + b)
+    cases = [
+        (t1 - t2, X2, a + b),                                          # a difference: |a| + |b|
+        (3 * (t1 - t1 ** 2), X1, 3 * (x + x ** 2)),                     # a scaled difference
+        ((1 + t1) ** -2 - 1, X1, (1 + x) ** -2 + 1),
+        (sp.log(1 + t1), X1, np.log1p(x) + 1),                          # log of a sum without cancellation
+        (sp.log(t1 + t2) ** 2, X2, L ** 2 + 2 * np.abs(L)),             # first order: 2|L| dL + L^2 u
+        ((t1 - t2) ** -1, X2, (a + b) / (a - b) ** 2),                  # a cancelling base inverted
+        (sp.log(t1 - t2), X2, np.abs(np.log(a - b)) + (a + b) / (a - b)),
+        ((t1 - t2) ** 2, X2, (a - b) ** 2 * (1 + 2 * ((a + b) / (a - b) - 1))),
+    ]
+    for k, (e, X, ref) in enumerate(cases):
+        got = _magnitude(e, X)
+        assert np.allclose(got, ref, rtol=1e-12, atol=0), (k, got, ref)
+
+
+def test_magnitude_of_the_subtraction_form():
+    """(g(t) - g(0)) / t with g = 1/(1+t): f = -1/(1+t) exactly, while the two terms of
+    the difference have magnitude 1/(1+t) and 1, so kappa = M/|f| = 2 + t grows like
+    2/t as t -> 0 -- the cancellation the per-point tolerance has to allow for."""
+    t = S.tsym(1)
+    e = ((1 + t) ** -1 - 1) / t
+    for x in (0.5, 1e-3, 2.0 ** -20, 2.0 ** -40):
+        M = _magnitude(e, [[x]])[0]
+        f = -1 / (1 + x)
+        assert math.isclose(M, (1 / (1 + x) + 1) / x, rel_tol=1e-12)
+        assert math.isclose(M / abs(f), (2 + x) / x, rel_tol=1e-12)
+
+
+def test_magnitude_bounds_the_value_and_is_homogeneous():
+    """M >= |f| on every unit of the bubble and the box and a sample of the double box,
+    at interior and boundary points; M(c f) = |c| M(f)."""
+    rng = np.random.default_rng(17)
+    for name, k in (("bubble", None), ("box", None), ("double_box", 24)):
+        orc = P.feynman_problem(getattr(W, name)())
+        units = orc.units if k is None else [orc.units[i] for i in rng.choice(len(orc.units), k, replace=False)]
+        for u in units:
+            X = np.concatenate([rng.uniform(size=(64, u.dim)),
+                                np.exp2(-rng.uniform(0, 40, size=(32, u.dim)))])
+            f = u.f_numpy(X)
+            M = P.magnitude_numpy(u, X)
+            ok = np.isfinite(f)
+            assert np.all(M[ok] >= np.abs(f[ok]) * (1 - 1e-12)), (name, u.sector, u.order)
+            scaled = P.Unit(u.sector, u.order, u.variables, -7 * u.expr)
+            assert np.allclose(P.magnitude_numpy(scaled, X[:8]), 7 * M[:8], rtol=1e-12)
