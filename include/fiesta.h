@@ -103,7 +103,9 @@ typedef struct {
     int32_t no_graph;         /* nonzero: launch directly instead of replaying the iteration loop as a
                                  CUDA graph (captured on the first call, reused while the call's
                                  parameters are unchanged) */
-    int32_t reserved;
+    int32_t accumulate;       /* units with several results: where the per-thread sums of the evaluation
+                                 kernel live; 0 = autotuned, 1 = registers, 2 = shared memory (both
+                                 variants give the same sums up to rounding order) */
     double small_x;           /* extended precision near the boundary (the paper's mixed mode, Sec. 4.6,
                                  SmallX), where the subtraction terms cancel: > 0 evaluates every
                                  point of a binary64 unit with a coordinate below small_x in
@@ -319,17 +321,28 @@ int fiesta_probe_peaks(double *out, int32_t n);
  * fiesta_integrate with adapt = 0, and writes each unit's sample mean of
  * v = f*J to mean[k] and its variance of the mean to var[k], k = unit -
  * unit_begin.  mean and var are caller-owned, both host or both device arrays.
+ * The context's device must be the current device.
  *
- * Its scratch (partial sums, counters) is one file-scope device array of about
- * 2.1 MB that every GPU loading the library keeps until the process exits.
- * Limits: at most 16384 units and 65536 work items (items of 2048 points) per
- * call; larger requests return FIESTA_E_INVALID with the sizes in the message.
- * The first call on each device looks up the array's device address (a CUDA
- * runtime query, no allocation); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents;
- * the parts that must start at zero are cleared by each call.  Calls whose
- * work overlaps on the GPU (other streams, other threads) race on the array.
- * Errors: FIESTA_E_INVALID, FIESTA_E_CUDA, FIESTA_E_NOMEM (shared memory).
+ * Non-finite samples count as zero, as in fiesta_integrate.  With host arrays
+ * the call waits for the GPU and then returns FIESTA_E_NONFINITE (the first such
+ * unit named in the message; mean and var are still written).  With device
+ * arrays the call does not wait, so it cannot return that status: instead the
+ * variance of every unit whose samples were not all finite is set to NaN.  Host
+ * arrays need that wait, which stream capture forbids: during a capture only
+ * device arrays are accepted.
+ *
+ * Its scratch (partial sums, counters) is one file-scope device array of
+ * 1 966 112 bytes (about 1.97 MB) that every GPU loading the library keeps until
+ * the process exits.  Limits: at most 16384 units and 65536 work items (items
+ * of 2048 points) per call; larger requests return FIESTA_E_INVALID with the
+ * sizes in the message.  The first call on each device looks up the array's
+ * device address (a CUDA runtime query, no allocation); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents; the parts that must start at zero are cleared by each call.
+ * Calls whose work overlaps on the GPU (other streams, other threads) race on
+ * the array.
+ * Errors: FIESTA_E_INVALID, FIESTA_E_CUDA, FIESTA_E_NOMEM (shared memory),
+ * FIESTA_E_NONFINITE (host arrays only).
  */
 int fiesta_sample_noalloc(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end, int64_t points, uint64_t seed,
                           int32_t iteration, int32_t precision, int32_t rng, double *mean, double *var);

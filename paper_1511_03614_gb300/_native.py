@@ -38,7 +38,7 @@ class Options(C.Structure):
                 ("unit_end", C.c_int64), ("timeout_ms", C.c_int64), ("threads", C.c_int32),
                 ("reset_grid", C.c_int32), ("iter_offset", C.c_int32), ("points_per_thread", C.c_int32),
                 ("probe_points", C.c_int64), ("fp32_budget", C.c_double), ("no_graph", C.c_int32),
-                ("reserved", C.c_int32), ("small_x", C.c_double),
+                ("accumulate", C.c_int32), ("small_x", C.c_double),
                 ("unit_points", C.POINTER(C.c_int64)), ("small_x32", C.c_double)]
 
 

@@ -111,7 +111,8 @@ class Integrator:
     def integrate(self, n_iter=10, points=100_000, seed=1, rng="philox", precision="fp64", adapt=True,
                   alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
                   iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
-                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0, unit_points=None, small_x32=0.0):
+                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0, unit_points=None, small_x32=0.0,
+                  accumulate="auto"):
         lo = min(u.order for u in self.prep.units)
         hi = max(u.order + _n_orders(u) - 1 for u in self.prep.units)
         nord = hi - lo + 1
@@ -119,7 +120,8 @@ class Integrator:
         opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(adapt), int(points),
                         int(seed) & 0xFFFFFFFFFFFFFFFF, float(alpha), int(bool(skip_first)), lo, int(b), int(e),
                         int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset),
-                        int(points_per_thread), int(probe_points), float(fp32_budget), int(not graph), 0,
+                        int(points_per_thread), int(probe_points), float(fp32_budget), int(not graph),
+                        {"auto": 0, "registers": 1, "shared": 2}[accumulate],
                         float(small_x), None, float(small_x32))
         if unit_points is not None:
             upts = np.ascontiguousarray(unit_points, dtype=np.int64)
