@@ -1,6 +1,7 @@
 """Build the CUDA library in-tree: nvcc for sm_103a, one translation unit."""
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 
@@ -21,7 +22,8 @@ def nvcc():
 
 def build(force=False, verbose=False):
     """Compile libfiesta_gb300.so next to this file if a source is newer (or force)."""
-    deps = SOURCES + [os.path.join(ROOT, "include", "fiesta.h")]
+    deps = SOURCES + [os.path.join(ROOT, "include", "fiesta.h")] + \
+        sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh")))
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(s) <= t for s in deps):

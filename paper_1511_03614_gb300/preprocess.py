@@ -113,6 +113,12 @@ def _mix_units(secs, real, Ks_of, group, max_slots=72):
             return None
         return Unit(run[0], Ks[0], d, prog, 0, n_out=len(Ks), sectors=tuple(run))
 
+    def build_one(i):
+        u = build([i])
+        if u is None:
+            raise ValueError(f"a fused unit holds at most {MAX_OUT} orders")
+        return u
+
     units, run, best = [], [], None
     for i in real:
         if not Ks_of(secs[i]):
@@ -120,10 +126,10 @@ def _mix_units(secs, real, Ks_of, group, max_slots=72):
         if run and (len(run) == group or len(secs[i].variables) != len(secs[run[0]].variables)):
             units.append(best)
             run, best = [], None
-        trial = build(run + [i])
+        trial = build(run + [i]) if run else build_one(i)
         if trial is None:                  # the group is full: start a new one with i
             units.append(best)
-            run, best = [i], build([i])
+            run, best = [i], build_one(i)
         else:
             run, best = run + [i], trial
     if best is not None:

@@ -80,3 +80,32 @@ def test_noalloc_pass_rejects_oversized_requests():
                                    m.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p))
     assert rc == -1
     assert b"maximum is 65536" in lib.fiesta_last_error()
+
+
+def test_noalloc_pass_reports_nonfinite_samples():
+    """A NaN constant planted on the host in one program: with host outputs the pass
+    returns FIESTA_E_NONFINITE naming the unit (as fiesta_integrate does), with device
+    outputs it marks that unit's variance NaN; a clean unit beside it is unaffected."""
+    torch, N, _, _ = _setup()
+    from paper_1511_03614_gb300 import parse_text, Integrator
+    lib = N.load()
+    prep = parse_text("1; 0; x[1]*0.5 + 1.0; |")
+    prep.units.append(parse_text("1; 0; x[1]*0.5 + 1.0; |").units[0])
+    prep.units[1].program.consts[:] = np.nan
+    for k, u in enumerate(prep.units):
+        u.rng_key = k
+    integ = Integrator(prep)
+    m = np.full(2, -1.0)
+    v = np.full(2, -1.0)
+    rc = lib.fiesta_sample_noalloc(integ.ctx, 0, 2, 10_000, 3, 0, 0, 0,
+                                   m.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p))
+    assert rc == -5 and b"unit 1" in lib.fiesta_last_error()
+    assert abs(m[0] - 0.75) < 1e-2 and np.isfinite(v[0]) and m[1] == 0.0
+    md = torch.zeros(2, dtype=torch.float64, device="cuda")
+    vd = torch.zeros(2, dtype=torch.float64, device="cuda")
+    rc = lib.fiesta_sample_noalloc(integ.ctx, 0, 2, 10_000, 3, 0, 0, 0,
+                                   C.c_void_p(md.data_ptr()), C.c_void_p(vd.data_ptr()))
+    assert rc == 0, lib.fiesta_last_error()
+    vh = vd.cpu().numpy()
+    assert np.isfinite(vh[0]) and np.isnan(vh[1]) and abs(md[0].item() - m[0]) <= 1e-12 * abs(m[0])
+    integ.close()
