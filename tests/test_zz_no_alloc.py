@@ -100,7 +100,7 @@ def test_noalloc_pass_reports_nonfinite_samples():
     rc = lib.fiesta_sample_noalloc(integ.ctx, 0, 2, 10_000, 3, 0, 0, 0,
                                    m.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p))
     assert rc == -5 and b"unit 1" in lib.fiesta_last_error()
-    assert abs(m[0] - 0.75) < 1e-2 and np.isfinite(v[0]) and m[1] == 0.0
+    assert abs(m[0] - 1.25) < 1e-2 and np.isfinite(v[0]) and m[1] == 0.0
     md = torch.zeros(2, dtype=torch.float64, device="cuda")
     vd = torch.zeros(2, dtype=torch.float64, device="cuda")
     rc = lib.fiesta_sample_noalloc(integ.ctx, 0, 2, 10_000, 3, 0, 0, 0,
