@@ -1,21 +1,23 @@
 """Throughput benchmark of the sector-integrand Monte-Carlo hot path.
 
-One step = one pass of the whole hot path over one workload: every
-(sector, eps order) integrand of the one-loop massless box at s = -1, t = -2
-(orders eps^-2..eps^0, 12 sectors of 3 dims, 32 integrands) integrated with
-Vegas, 10 iterations x 10^6 Philox points (10^7 points per sector per order),
-binary64: point generation, Vegas map, bytecode evaluation, reduction, grid
-refinement and the per-order assembly.  By default each sector is one fused
-unit that evaluates all its orders at every point (--fuse 0: one unit per
-sector and order); the metric counts evaluations of (sector, order) integrands.
+One step = one pass of the whole hot path over one workload.  Default: the
+two-loop massless planar double box at s = t = -1 (orders eps^-4..eps^0, 293
+sectors of 6 dimensions, 1141 (sector, eps order) integrands), one unit per
+sector evaluating all its orders at every point (--fuse 0: one unit per sector
+and order), one Vegas iteration of 10^7 Philox points per sector, binary64:
+point generation, Vegas map, bytecode evaluation, reduction, grid refinement
+and the per-order assembly.  The metric counts evaluations of (sector, order)
+integrands.  --workload box|bubble|box_physical|stress selects the other
+configurations.
 
 Prints one JSON line (rank 0).  After the timed region the line also carries
 ``time_to_1e-4``: GPU-seconds to 1e-4 relative error on every order, plain
-binary64 Vegas against randomised QMC, AUTO precision with allocation and the
-cubature, measured live (--no-tta skips it).  ``--mode tta`` runs the same
-comparison with more forms on any workload, ``--mode cuhre`` the cubature's
-evaluation rate.  ``--impl reference`` times the oracle (the plain CPU
-restatement of the method) on a bounded sample of the same workload.
+binary64 Vegas against the faster forms (randomised QMC, AUTO precision with
+point allocation, the learned flow on the double box, the cubature on the
+box), measured live (--no-tta skips it).  ``--mode tta`` runs the comparison
+with more forms on any workload, ``--mode cuhre`` the cubature's evaluation
+rate.  ``--impl reference`` times the oracle (the plain CPU restatement of the
+method) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -37,7 +39,7 @@ WORKLOADS = {
     "box": (1_000_000, 10, "philox"),
     "bubble": (100_000, 10, "philox"),
     "box_physical": (1_000_000, 10, "philox"),
-    "double_box": (1_000_000, 1, "philox"),
+    "double_box": (10_000_000, 1, "philox"),
     "stress": (1 << 20, 1, "sobol"),
 }
 
@@ -48,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="box", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="double_box", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "auto"])
     ap.add_argument("--points", type=int, default=0, help="points per unit per iteration (0: workload default)")
     ap.add_argument("--iters", type=int, default=0, help="Vegas iterations per step (0: workload default)")
@@ -170,16 +172,19 @@ def op_costs(peaks):
     return {"LOG": log_c, "DIV": div_c, "INV": div_c, "ATAN2": atan_c}
 
 
-def unit_work(prog, costs, dim, adapt):
-    """(algorithmic flops, FMA-equivalent pipe slots) per point of one unit.
+def unit_work(prog, costs, dim, n_out):
+    """Work per point of one unit: (algorithmic flops, FMA-equivalent pipe slots,
+    flops of the integrand body alone).
 
-    Flops: ADD SUB MUL NEG ADDC MULC = 1, MAC MACC = 2, POWI = its multiplies,
-    DIV INV LOG ATAN2 = 1; plus the Vegas map (4 per coordinate: scale, edge difference,
-    interpolation FMA, Jacobian product) and the accumulation (v = f J, v^2, two
-    sums: 4).  Pipe slots weigh LOG/DIV/INV/ATAN2 by their measured cost.
+    Flops follow the survey's count: ADD SUB MUL NEG ADDC MULC = 1, MAC MACC (fused
+    multiply-add) = 2, POWI = its multiplies, and LOG DIV INV ATAN2 converted at their
+    measured cost (FMA slots x 2 flops; ``op_costs``); plus the Vegas map (4 per
+    coordinate) and the reduction (3 per result: v = f J, sum v, sum v^2).  Pipe slots
+    count every instruction of the body as one FMA slot (the special operations at
+    their measured cost), so slots x 2 / time is the pipe's occupancy, a different
+    figure from the flop rate.
     """
     c = prog.counts
-    flops = prog.flops()
     powi = 0
     for w in prog.code.tolist():
         if (w & 0xFF) == 12:
@@ -187,11 +192,77 @@ def unit_work(prog, costs, dim, adapt):
             e = e - 256 if e >= 128 else e
             m = abs(e)
             powi += max(m.bit_length() - 1 + bin(m).count("1") - 1, 0) + (1 if e < 0 else 0)
-    flops += powi + c.get("DIV", 0) + c.get("INV", 0) + c.get("LOG", 0) + c.get("ATAN2", 0)
-    slots = prog.flops() / 1.0 - (c.get("MAC", 0) + c.get("MACC", 0)) + powi + \
-        sum(costs[k] * c.get(k, 0) for k in ("LOG", "DIV", "INV", "ATAN2"))
-    extra = 4 * dim + 4
-    return flops + extra, slots + extra
+    special = sum(costs[k] * c.get(k, 0) for k in ("LOG", "DIV", "INV", "ATAN2"))
+    body = prog.flops() + powi + 2.0 * special
+    slots = prog.flops() - (c.get("MAC", 0) + c.get("MACC", 0)) + powi + special
+    extra = 4 * dim + 3 * n_out
+    return body + extra, slots + extra, body
+
+
+def op_costs32(peaks):
+    """binary32 FMA-equivalents of logf and of the binary32 divide (atan2f: as logf)."""
+    fma_rate = peaks[3] * 1e12 / 2.0
+    log_c = fma_rate / (peaks[4] * 1e9)
+    div_c = fma_rate / (peaks[5] * 1e9)
+    return {"LOG": log_c, "DIV": div_c, "INV": div_c, "ATAN2": log_c}
+
+
+# DRAM bytes (read + write) per launch of the evaluation kernel from ncu captures, by
+# (workload, precision, fused); the kernel stages programs, constants and grids in shared
+# memory, so this does not grow with the number of points.  None: not captured for
+# the current kernel.
+TRAFFIC = {("box", "fp64", True): (110336, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                             "k_eval<double, Philox, 6> launch on the fused box (12 units x 2e5 "
+                                             "points)")}
+
+
+def roofline_of(prep, res, peaks, pts, pass_s, args, iters):
+    """Roofline of the evaluation kernel (alu-bound: the binary64 pipe for binary64
+    units; for binary32 units the binary32 pipe carries the body and the map, the
+    binary64 pipe the reduction).  achieved = algorithmic flops per pass / pass time on
+    the binding pipe; the other pipe's utilisation and the binary64 FMA-slot occupancy
+    are reported beside it."""
+    costs, costs32 = op_costs(peaks), op_costs32(peaks)
+    prec = {}
+    if res is not None:
+        for d in res.per_unit:
+            prec[d["unit"]] = d["precision"]
+    f64 = f32 = slots64 = 0.0
+    for k, u in enumerate(prep.units):
+        if prec.get(k, "fp64") == "fp32":
+            _, _, body = unit_work(u.program, costs32, u.dim, u.n_out)
+            f32 += body + 4 * u.dim
+            f64 += 3 * u.n_out
+            slots64 += 3 * u.n_out
+        else:
+            fl, sl, _ = unit_work(u.program, costs, u.dim, u.n_out)
+            f64 += fl
+            slots64 += sl
+    f64, f32, slots64 = f64 * pts, f32 * pts, slots64 * pts
+    t64 = f64 / (peaks[0] * 1e12)
+    t32 = f32 / (peaks[3] * 1e12)
+    fp64_bound = t64 >= t32
+    achieved = (f64 if fp64_bound else f32) / pass_s * 1e-12
+    peak = peaks[0] if fp64_bound else peaks[3]
+    key = (args.workload, args.precision, bool(args.fuse))
+    traffic = TRAFFIC.get(key)
+    return {"bound": "alu", "pipe": "fp64" if fp64_bound else "fp32", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic[0] if traffic else None, "traffic_source": traffic[1] if traffic else None,
+            "kernel": "k_eval",
+            "work": "flops per evaluation pass: add/sub/mul 1, fma 2, log/div/atan2 at their measured cost in "
+                    "FMA slots x 2, map 4 per coordinate, reduction 3 per result",
+            "peak_source": "measured in-process (fiesta_probe_peaks): binary64 / binary32 FMA rate",
+            "nominal_fp64_tflops": 1.25,
+            "pipes": {"fp64": {"tflop_per_pass": f64 * 1e-12, "utilisation": t64 / pass_s},
+                      "fp32": {"tflop_per_pass": f32 * 1e-12, "utilisation": t32 / pass_s}},
+            "fma_slot_occupancy": 2.0 * slots64 / pass_s / (peaks[0] * 1e12),
+            "eval_ms_per_pass": pass_s * 1e3,
+            "eval_launches_per_pass": res.stats["eval_launches"] // max(iters, 1) if res else None,
+            "peaks_measured": {"fp64_tflops": peaks[0], "fp64_log_cuda_gps": peaks[1], "fp64_div_gps": peaks[2],
+                               "fp32_tflops": peaks[3], "fp32_log_gps": peaks[4], "fp32_div_gps": peaks[5],
+                               "fp64_log_table_gps": peaks[6], "fp64_atan2_gps": peaks[7]},
+            "op_costs_fma_slots": {"fp64": costs, "fp32": costs32}}
 
 
 def run_ours(args):
@@ -212,7 +283,10 @@ def run_ours(args):
     peaks = list(peaks)
     integ = Integrator(prep)
     # replicas: every rank integrates every unit with its own point streams (weak scaling)
-    kw = dict(n_iter=iters, points=pts, seed=1 + rank, rng=rng, precision=args.precision)
+    # one iteration per step refines the grid after it (adapt=2), so every step runs
+    # every row of the path: points, map, evaluation, reduction, refinement, assembly
+    kw = dict(n_iter=iters, points=pts, seed=1 + rank, rng=rng, precision=args.precision,
+              adapt=2 if iters == 1 else True)
     for _ in range(args.warmup):
         integ.integrate(**kw)
     torch.cuda.synchronize()
@@ -245,34 +319,9 @@ def run_ours(args):
     all_points = sum_over_ranks(points, world)
     value = all_points / (t_max * 1e-3)
 
-    # roofline of the evaluation kernel (dominant): algorithmic work per evaluation pass (one
-    # launch per iteration, or one per slot-size class when programs differ widely in size)
-    costs = op_costs(peaks)
-    per_unit = [unit_work(u.program, costs, u.dim, True) for u in prep.units]
-    flops_per_launch = sum(f for f, _ in per_unit) * pts
-    slots_per_launch = sum(s for _, s in per_unit) * pts
-    avg_eval_s = eval_ms / max(eval_iters, 1) * 1e-3     # the evaluation kernel's time per iteration
-    achieved = 2.0 * slots_per_launch / avg_eval_s * 1e-12          # FMA-equivalent TFLOP/s
-    peak_meas = peaks[0]
-    nominal = 1.25
-    # DRAM bytes per launch of the evaluation kernel from an ncu capture (read + write); the
-    # kernel stages programs, constants and grids in shared memory, so this does not grow
-    # with the number of points
-    traffic = 110336 if (args.workload == "box" and args.precision == "fp64" and args.fuse) else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "TFLOP/s",
-                "frac": achieved / peak_meas, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_eval<double, Philox, 6> "
-                                  "on the fused box (12 units x 2e5 points, one launch)" if traffic else None,
-                "kernel": "k_eval", "work": "FMA-equivalent pipe slots x 2 per evaluation pass (log/div weighted by "
-                "measured cost)", "peak_source": "measured in-process (fiesta_probe_peaks)",
-                "nominal_fp64_tflops": nominal,
-                "algorithmic_tflops": flops_per_launch / avg_eval_s * 1e-12,
-                "eval_ms_per_pass": avg_eval_s * 1e3,
-                "eval_launches_per_pass": res.stats["eval_launches"] // max(iters, 1) if res else None,
-                "peaks_measured": {"fp64_tflops": peaks[0], "fp64_log_cuda_gps": peaks[1], "fp64_div_gps": peaks[2],
-                                   "fp32_tflops": peaks[3], "fp32_log_gps": peaks[4], "fp32_div_gps": peaks[5],
-                                   "fp64_log_table_gps": peaks[6], "fp64_atan2_gps": peaks[7]},
-                "op_costs_fma_slots": costs}
+    # roofline of the evaluation kernel (dominant): algorithmic work per evaluation pass
+    # (one pass per iteration) over the pass's mean CUDA-event duration
+    roofline = roofline_of(prep, res, peaks, pts, eval_ms / max(eval_iters, 1) * 1e-3, args, iters)
 
     # end to end through the public API with host buffers: upload programs, integrate,
     # read the per-order results back; the copies are inside the timed region.
@@ -304,7 +353,8 @@ def run_ours(args):
     # GPU-seconds to 1e-4 relative error on every eps order, plain binary64 Vegas against
     # the faster forms (randomised QMC, per-unit binary32 with allocation, cubature)
     tta = None
-    if rank == 0 and world == 1 and not args.no_tta and args.workload in ("box", "bubble", "box_physical"):
+    if rank == 0 and world == 1 and not args.no_tta and args.workload in ("box", "bubble", "box_physical",
+                                                                         "double_box"):
         tta = time_to_accuracy(args.workload, 1e-4)
 
     if rank == 0:
@@ -321,7 +371,10 @@ def run_ours(args):
                                     "box_physical": "one-loop massless box at the physical point s=3 t=-1 (F changes "
                                                     "sign): contour deformation, complex results, eps^-2..eps^0, "
                                                     "12 sectors x 3 dims, Vegas 10 it x 1e6 Philox points per unit",
-                                    "double_box": "planar double box s=t=-1, eps^-4..eps^0, 293 sectors x 6 dims",
+                                    "double_box": "two-loop massless planar double box s=t=-1, eps^-4..eps^0, "
+                                                  "293 sectors x 6 dims (1141 sector-order integrands), Vegas 1 it "
+                                                  "x 1e7 Philox points per sector per step, grid refined after it "
+                                                  "(20 steps: 2e8 points per sector)",
                                     "stress": "10000 seeded synthetic integrands, dims 3..8, 2^20 Sobol points"
                                     }[args.workload],
                        "units": len(prep.units), "points_per_unit_per_iter": pts, "iterations": iters,
@@ -347,31 +400,59 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def time_to_accuracy(workload, target):
+def time_to_accuracy(workload, target, cap_s=15.0):
     """GPU-seconds (the library's device time) to `target` relative error on every eps
-    order: plain binary64 Vegas (one unit per sector and order) against randomised QMC
-    on the adapted grids, AUTO precision with point allocation, and the cubature (both
-    on fused units).  Errors are reported, not raised: this is an addition to the line."""
+    order: plain binary64 Vegas (one unit per sector and order) against the faster forms.
+    Box-sized workloads: randomised QMC on the adapted grids, AUTO precision with point
+    allocation, and the cubature (fused units).  Double box: randomised QMC, AUTO with
+    allocation and the learned flow (fused units, binary32 body); forms that do not
+    converge within ``cap_s`` GPU-seconds report the device time spent, the worst
+    error/target ratio and an extrapolation gpu_s * ratio^2 (errors fall as the inverse
+    square root of the points once the grids have settled), labelled as such.  Errors
+    are reported, not raised: this is an addition to the line."""
     from paper_1511_03614_gb300 import Integrator
-    from paper_1511_03614_gb300.api import run_to_accuracy, run_to_accuracy_rqmc, run_cuhre_to_accuracy
+    from paper_1511_03614_gb300.api import run_to_accuracy, run_to_accuracy_rqmc, run_cuhre_to_accuracy, run_flow
     out = {"target": target, "unit": "GPU-s", "workload": workload}
-    runs = (("fp64_vegas", False, lambda ig: run_to_accuracy(ig, target=target, points=1_000_000, max_iters=200)),
-            ("rqmc_fp64", True, lambda ig: run_to_accuracy_rqmc(ig, target=target, points=1 << 18,
-                                                                max_points=1 << 22)),
-            ("auto_alloc", False, lambda ig: run_to_accuracy(ig, target=target, points=1_000_000, max_iters=200,
-                                                             precision="auto", allocate=True)),
-            ("cuhre_fp64", True, lambda ig: run_cuhre_to_accuracy(ig, target=target)))
+    if workload == "double_box":
+        cap = dict(max_gpu_s=cap_s)
+        runs = (("fp64_vegas", False, lambda ig: run_to_accuracy(ig, target=target, points=2_000_000,
+                                                                 max_iters=400, **cap)),
+                ("rqmc_fp64", True, lambda ig: run_to_accuracy_rqmc(ig, target=target, points=1 << 18,
+                                                                    max_points=1 << 22)),
+                ("auto_alloc", False, lambda ig: run_to_accuracy(ig, target=target, points=2_000_000,
+                                                                 max_iters=400, precision="auto", allocate=True,
+                                                                 **cap)),
+                ("flow_fp32", True, lambda ig: run_flow(ig, target=target, points=2_000_000, keep=4096,
+                                                        train_rounds=8, steps_per_round=20, max_rounds=300,
+                                                        precision="fp32", **cap)))
+    else:
+        runs = (("fp64_vegas", False, lambda ig: run_to_accuracy(ig, target=target, points=1_000_000,
+                                                                 max_iters=200)),
+                ("rqmc_fp64", True, lambda ig: run_to_accuracy_rqmc(ig, target=target, points=1 << 18,
+                                                                    max_points=1 << 22)),
+                ("auto_alloc", False, lambda ig: run_to_accuracy(ig, target=target, points=1_000_000,
+                                                                 max_iters=200, precision="auto", allocate=True)),
+                ("cuhre_fp64", True, lambda ig: run_cuhre_to_accuracy(ig, target=target)))
     for name, fuse, fn in runs:
         try:
+            t0 = time.perf_counter()
             ig = Integrator(prepared(workload, fuse=fuse))
             r = fn(ig)
-            out[name] = {"gpu_s": r["gpu_s"], "converged": r["converged"]}
+            rec = {"gpu_s": r["gpu_s"], "converged": r["converged"], "wall_s": time.perf_counter() - t0}
+            if not r["converged"] and r.get("ratio"):
+                rec["error_over_target"] = r["ratio"]
+                rec["extrapolated_gpu_s"] = r["gpu_s"] * r["ratio"] ** 2
+            rec["values"] = {str(n): [_num(r["values"][n]), _num(r["errors"][n])] for n in r["values"]}
+            out[name] = rec
             ig.close()
         except Exception as e:          # noqa: BLE001 - reported in the line instead
             out[name] = {"error": str(e)[:200]}
-    base = out.get("fp64_vegas", {}).get("gpu_s")
-    out["speedup_vs_fp64_vegas"] = {k: base / v["gpu_s"] for k, v in out.items()
-                                    if isinstance(v, dict) and v.get("gpu_s") and base and k != "fp64_vegas"}
+    base = out.get("fp64_vegas", {})
+    base_s = base.get("gpu_s") if base.get("converged") else base.get("extrapolated_gpu_s")
+    out["speedup_vs_fp64_vegas"] = {k: base_s / v["gpu_s"] for k, v in out.items()
+                                    if isinstance(v, dict) and v.get("converged") and base_s and k != "fp64_vegas"}
+    if base_s and not base.get("converged"):
+        out["speedup_basis"] = "fp64_vegas extrapolated from its capped run"
     return out
 
 

@@ -448,7 +448,7 @@ def allocate_points(prep, sig, n_used, values, target, floor, points, lo_frac=0.
 
 def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_iters=200, seed=1,
                     precision="fp64", rng="philox", floor=1e-2, skip_first=1, checkpoint=None, resume=None,
-                    stop_after=None, allocate=False, small_x=0.0, small_x32=0.0):
+                    stop_after=None, allocate=False, small_x=0.0, small_x32=0.0, max_gpu_s=None):
     """Vegas until every eps order of the assembled result has sigma <= target * max(|R|, floor * max|R|).
 
     Iterations are combined per unit with inverse-variance weights across calls
@@ -463,7 +463,8 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
     every call after the first where the variance is (``allocate_points``) instead of
     evenly; the total points per iteration stay nu * points.  ``small_x`` /
     ``small_x32`` promote points near the boundary of binary64 / binary32 units one
-    precision level (see fiesta_options).
+    precision level (see fiesta_options).  ``max_gpu_s`` stops once that much device
+    time is spent; ``ratio`` in the result is max over orders of error / target.
     """
     prep = integ.prep
     recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
@@ -506,14 +507,21 @@ def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_
         sig = np.sqrt(1.0 / sw)
         R, E, values = _assembled(prep, recs, val, sig)
         big = max(abs(v) for v in R.values())
-        ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)
+        ratio = _worst_ratio(R, E, target, floor)
+        ok = ratio <= 1.0
         res = dict(gpu_s=gpu_ms * 1e-3, points=points_done, iterations=it, values=R, errors=E, converged=ok,
-                   unit_values=val.copy(), unit_sigmas=sig.copy())
-        if ok or (stop_after is not None and it >= stop_after):
+                   unit_values=val.copy(), unit_sigmas=sig.copy(), ratio=ratio)
+        if ok or (stop_after is not None and it >= stop_after) or (max_gpu_s and gpu_ms * 1e-3 >= max_gpu_s):
             break
         if allocate and np.all(n_used > 0):
             unit_pts = allocate_points(prep, sig, n_used, values, target, floor, points)
     return res
+
+
+def _worst_ratio(R, E, target, floor):
+    """max over eps orders n of |error_n| / (target * max(|R_n|, floor * max_k |R_k|))."""
+    big = max(abs(v) for v in R.values())
+    return max(abs(E[n]) / (target * max(abs(R[n]), floor * big)) for n in R)
 
 
 def run_cuhre_to_accuracy(integ, target=1e-4, floor=1e-2, rel_tol=None, shrink=0.1, max_rounds=6, max_passes=60,
@@ -583,10 +591,10 @@ def run_to_accuracy_rqmc(integ, target=1e-4, points=1 << 18, replicates=8, adapt
         val = swi / sw
         sig = np.sqrt(1.0 / sw)
         R, E, values = _assembled(prep, recs, val, sig)
-        big = max(abs(v) for v in R.values())
-        ok = all(abs(E[n_]) <= target * max(abs(R[n_]), floor * big) for n_ in R)
+        ratio = _worst_ratio(R, E, target, floor)
+        ok = ratio <= 1.0
         res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=rnd + 1, points_per_replicate=n, values=R, errors=E,
-                   converged=ok, unit_values=val.copy(), unit_sigmas=sig.copy())
+                   converged=ok, unit_values=val.copy(), unit_sigmas=sig.copy(), ratio=ratio)
         if ok or 2 * n > max_points:
             break
         n *= 2
@@ -594,7 +602,7 @@ def run_to_accuracy_rqmc(integ, target=1e-4, points=1 << 18, replicates=8, adapt
 
 
 def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, steps_per_round=20, lr=2e-3,
-             power=1, max_rounds=200, seed=1, precision="fp32", floor=1e-2, skip_rounds=None):
+             power=1, max_rounds=200, seed=1, precision="fp32", floor=1e-2, skip_rounds=None, max_gpu_s=None):
     """Learned proposal: per unit, alternate flow sampling (an unbiased estimate each
     round) and training on the round's kept points; stop when every eps order meets
     the target (same rule as run_to_accuracy).  Rounds while training are combined
@@ -626,10 +634,10 @@ def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, st
         val = swi / sw
         sig = np.sqrt(1.0 / sw)
         R, E, values = _assembled(prep, recs, val, sig)
-        big = max(abs(x) for x in R.values())
-        ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)
+        ratio = _worst_ratio(R, E, target, floor)
+        ok = ratio <= 1.0
         res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=r + 1, values=R, errors=E, converged=ok,
-                   unit_values=val.copy(), unit_sigmas=sig.copy())
-        if ok and r >= train_rounds:
+                   unit_values=val.copy(), unit_sigmas=sig.copy(), ratio=ratio)
+        if (ok and r >= train_rounds) or (max_gpu_s and gpu_ms * 1e-3 >= max_gpu_s):
             break
     return res

@@ -150,27 +150,31 @@ def _schedule(nodes, live, outs):
     return out
 
 
-def emit(graph, out, dim):
+def emit(graph, out, dim, fuse_fma=True):
     """Lower the nodes reachable from ``out`` (one node or a list of result nodes) to a
-    Program (linear-scan slot allocation); results stay live to the end."""
+    Program (linear-scan slot allocation); results stay live to the end.  With
+    ``fuse_fma`` a product used only by one sum is first contracted into a fused
+    multiply-add (``ir.contract``)."""
     outs = list(out) if isinstance(out, (list, tuple)) else [out]
-    out = outs[0]
     nodes = graph.nodes
-    live = set()
-    stack = list(outs)
-    while stack:
-        i = stack.pop()
-        if i in live:
-            continue
-        live.add(i)
-        n = nodes[i]
-        if n[0] in ("add", "sub", "mul", "div", "atan2"):
-            stack += [n[1], n[2]]
-        elif n[0] == "fma":
-            stack += [n[1], n[2], n[3]]
-        elif n[0] in ("neg", "log", "inv", "powi"):
-            stack.append(n[1])
+
+    def live_set(roots):
+        live = set()
+        stack = list(roots)
+        while stack:
+            i = stack.pop()
+            if i in live:
+                continue
+            live.add(i)
+            stack += list(_args(nodes[i]))
+        return live
+
+    if fuse_fma:
+        from .ir import contract
+        outs = contract(graph, outs)
+    live = live_set(outs)
     order = _schedule(nodes, live, outs)
+    out = outs[0]
 
     consts = []
     cidx = {}

@@ -106,6 +106,49 @@ class _SectorEval:
         self._corner[key] = node
         return node
 
+    def inv_poly_at(self, i, W):
+        """1/P_i with t_W = 0.  When every coefficient of P_i is positive (each corner
+        value is then at least its constant term and bounded on the cube) the
+        reciprocals of all corner values of P_i are formed in batches of four with one
+        division (Montgomery's simultaneous inversion: prefix products p_k, r = 1/p_4,
+        then 1/v_k = r p_(k-1) and r <- r v_k going down), 3 multiplications per
+        further value instead of a division each; a product of four such values stays
+        well inside the binary32 range."""
+        key = ("invP", i, W)
+        if key in self._corner:
+            return self._corner[key]
+        g = self.g
+        if not all(c > 0 for c in self.sec.polys[i][0].values()):
+            self._corner[key] = g.inv(self.poly_at(i, W))
+            return self._corner[key]
+        corners = [tuple(sorted(w)) for w in _subsets(self.S)]
+        vals = []
+        for w in corners:
+            v = self.poly_at(i, w)
+            if v not in vals:
+                vals.append(v)
+        inv = {}
+        for k in range(0, len(vals), 4):
+            grp = vals[k:k + 4]
+            pre = [grp[0]]
+            for v in grp[1:]:
+                pre.append(g.mul(pre[-1], v))
+            r = g.inv(pre[-1])
+            for m in range(len(grp) - 1, 0, -1):
+                inv[grp[m]] = g.mul(r, pre[m - 1])
+                r = g.mul(r, grp[m])
+            inv[grp[0]] = r
+        for w in corners:
+            self._corner[("invP", i, w)] = inv[self.poly_at(i, w)]
+        return self._corner[key]
+
+    def _pow_at(self, i, W, e):
+        """P_i^e with t_W = 0 for an integer e (negative powers from the batched reciprocal)."""
+        e = int(e)
+        if e < 0:
+            return self.g.powi(self.inv_poly_at(i, W), -e)
+        return self.g.powi(self.poly_at(i, W), e)
+
     def logpoly_at(self, i, W):
         key = ("logP", i, W)
         if key not in self._corner:
@@ -122,20 +165,43 @@ class _SectorEval:
             out = g.c(1.0)
             for i, (p, (a0, a1)) in enumerate(self.sec.polys):
                 if a0:
-                    out = g.mul(out, g.powi(self.poly_at(i, W), a0))
+                    out = g.mul(out, self._pow_at(i, W, a0) if float(a0).is_integer()
+                                else g.powi(self.poly_at(i, W), a0))
             for i, power in self.sec.log_factor:
                 out = g.mul(out, g.powi(self.logpoly_at(i, W), power))
         else:
-            L = g.c(0.0)
-            for i, (p, (a0, a1)) in enumerate(self.sec.polys):
-                if a1:
-                    L = g.fma(self.logpoly_at(i, W), g.c(float(a1)), L)
+            L = self.L_at(W)
             if g.const_value(L) == 0.0:
                 out = g.c(0.0)
             else:
                 out = g.mul(g.mul(self.G_at(N - 1, W), L), g.c(1.0 / N))
         self._corner[key] = out
         return out
+
+    def L_at(self, W):
+        """L = sum_i a'_i log P_i at t_W = 0.  With integer a'_i (integer indices in
+        d = 4 - 2 eps) this is one logarithm, log prod_i P_i^a'_i, instead of one per
+        polynomial: the P_i are positive and bounded away from 0 and infinity on the
+        cube (each has a constant term, all coefficients positive when F > 0), so the
+        product stays in range, and its rounding error (a few u, relative) becomes the
+        same absolute error in L as the sum of logarithms carries."""
+        key = ("L", W)
+        if key in self._corner:
+            return self._corner[key]
+        g = self.g
+        terms = [(i, a1) for i, (p, (a0, a1)) in enumerate(self.sec.polys) if a1]
+        if terms and not self.sec.log_factor and all(float(a1).is_integer() for _, a1 in terms) and \
+                all(c > 0 for p, _ in self.sec.polys for c in p.values()):
+            prod = g.c(1.0)
+            for i, a1 in terms:
+                prod = g.mul(prod, self._pow_at(i, W, a1))
+            L = g.log(prod)
+        else:
+            L = g.c(0.0)
+            for i, a1 in terms:
+                L = g.fma(self.logpoly_at(i, W), g.c(float(a1)), L)
+        self._corner[key] = L
+        return L
 
     def D(self, T, N):
         """sum over Z subset S\\T of (-1)^|Z| G_N(t_{T u Z} = 0), by successive differences."""

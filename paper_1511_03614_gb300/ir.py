@@ -121,6 +121,11 @@ class Graph:
         return self._add(("neg", a))
 
     def powi(self, a, n):
+        """a^n for an integer n.  Exponents up to 16 in magnitude become products
+        (a^2k from a^k squared, a^(k+1) = a^k a; shared through the hash-consing), a
+        negative one the same products of 1/a, so every power of one base shares a
+        single reciprocal; larger exponents keep the POWI instruction."""
+        n = int(n)
         if n == 0:
             return self.c(1.0)
         if n == 1:
@@ -128,11 +133,15 @@ class Graph:
         ca = self.const_value(a)
         if ca is not None:
             return self.c(ca ** n)
-        if n == 2:
-            return self.mul(a, a)
+        if n < 0 and -n <= 16:
+            return self.powi(self.inv(a), -n)
         if n == -1:
             return self.inv(a)
-        return self._add(("powi", a, int(n)))
+        if 2 <= n <= 16:
+            h = self.powi(a, n // 2)
+            sq = self.mul(h, h)
+            return sq if n % 2 == 0 else self.mul(sq, a)
+        return self._add(("powi", a, n))
 
     def log(self, a):
         ca = self.const_value(a)
@@ -157,6 +166,100 @@ class Graph:
         for i in items:
             out = self.mul(out, i)
         return out
+
+
+def _children(n):
+    k = n[0]
+    if k in ("add", "sub", "mul", "div", "atan2"):
+        return (n[1], n[2])
+    if k == "fma":
+        return (n[1], n[2], n[3])
+    if k in ("neg", "log", "inv"):
+        return (n[1],)
+    if k == "powi":
+        return (n[1],)
+    return ()
+
+
+def contract(g, outs, allow=None):
+    """Fused multiply-add contraction of the nodes reachable from ``outs``: a product
+    used only by one sum becomes the multiply of a fused multiply-add there,
+    a*b + c -> fma(a, b, c) and c - a*k -> fma(a, -k, c) for a constant k.  The
+    value changes only by the rounding of the product that is no longer made; the
+    operation count of every such pair halves.  ``allow(sum_node, product_node,
+    other_node)`` (original node ids) can veto a contraction.  Returns the new
+    result nodes (in the same graph)."""
+    nodes = g.nodes
+    order, seen, stack = [], set(), list(outs)
+    while stack:                                  # post-order over the live nodes
+        i = stack[-1]
+        if i in seen:
+            stack.pop()
+            continue
+        pend = [a for a in _children(nodes[i]) if a not in seen]
+        if pend:
+            stack.extend(pend)
+            continue
+        seen.add(i)
+        order.append(i)
+        stack.pop()
+    uses = {}
+    for i in order:
+        for a in _children(nodes[i]):
+            uses[a] = uses.get(a, 0) + 1
+    for o in outs:
+        uses[o] = uses.get(o, 0) + 1
+    new = {}
+
+    def single_mul(orig):
+        n = nodes[orig]
+        return n[0] == "mul" and uses.get(orig, 0) == 1
+
+    def ok(i, m, other):
+        return allow is None or allow(i, m, other)
+
+    for i in order:
+        n = nodes[i]
+        k = n[0]
+        ch = [new[a] for a in _children(n)]
+        if k == "add":
+            a, b = n[1], n[2]
+            cands = [(m, o) for m, o in ((a, b), (b, a)) if single_mul(m) and ok(i, m, o)]
+            if cands:
+                m, other = cands[0]
+                mm = nodes[new[m]]
+                if mm[0] == "mul":
+                    new[i] = g.fma(mm[1], mm[2], new[other])
+                    continue
+            new[i] = g.add(ch[0], ch[1])
+        elif k == "sub":
+            a, b = n[1], n[2]
+            mm = nodes[new[b]]
+            if single_mul(b) and ok(i, b, a) and mm[0] == "mul" and (g.const_value(mm[1]) is not None or
+                                                                   g.const_value(mm[2]) is not None):
+                x, kc = (mm[2], mm[1]) if g.const_value(mm[1]) is not None else (mm[1], mm[2])
+                new[i] = g.fma(x, g.c(-g.const_value(kc)), new[a])
+                continue
+            new[i] = g.sub(ch[0], ch[1])
+        elif k == "mul":
+            new[i] = g.mul(ch[0], ch[1])
+        elif k == "fma":
+            new[i] = g.fma(ch[0], ch[1], ch[2])
+        elif k == "div":
+            new[i] = g.div(ch[0], ch[1])
+        elif k == "atan2":
+            new[i] = g.atan2(ch[0], ch[1])
+        elif k == "neg":
+            new[i] = g.neg(ch[0])
+        elif k == "log":
+            new[i] = g.log(ch[0])
+        elif k == "inv":
+            new[i] = g.inv(ch[0])
+        elif k == "powi":
+            new[i] = g._add(("powi", ch[0], n[2]))
+        else:
+            new[i] = i
+    return [new[o] for o in outs]
 
 
 # ---------------------------------------------------------------------------

@@ -18,7 +18,7 @@ import pytest
 import workloads as W
 from oracle import pipeline as P, vegas as V
 
-from gpu_common import need_gpu, feynman, feynman_fused, sample_points, reference, Parity
+from gpu_common import need_gpu, feynman, feynman_fused, sample_points, reference, Parity, C_SCALED, UROUND
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +72,10 @@ def test_fused_double_box_same_point_sums(accumulate, threads):
     """Iteration 0 on the uniform grid, every fused unit at once: each result's mean
     equals the oracle's Vegas estimate of that sector and order at the same Philox
     points, with the kernel's per-thread sums in registers (the variant the double-box
-    benchmark runs) and in shared memory."""
+    benchmark runs) and in shared memory.  Both means are binary64 sums of values that
+    each err by at most C_SCALED u M (the per-point bar), so they may differ by twice
+    that summed: 2 C_SCALED u mean(M |J|).  Double-box units cancel strongly (mean(M J)
+    reaches 1.7e5 mean|v| on the eps^0 result of a 4-subtraction sector)."""
     need_gpu()
     prep, idx = _dbox_fused_sample(n_total=16, seed=33)
     _, orc = feynman("double_box")
@@ -90,7 +93,8 @@ def test_fused_double_box_same_point_sums(accumulate, threads):
             o = by[(u.sector, u.order + k)]
             m, _ = integ.iterations(i, 1, k)
             v = o.f_numpy(X) * J
-            assert abs(m[0] - np.mean(v)) <= 1e-11 * np.mean(np.abs(v)), (int(i), k, m[0], np.mean(v))
+            bound = 2 * C_SCALED * UROUND["fp64"] * np.mean(P.magnitude_numpy(o, X) * np.abs(J))
+            assert abs(m[0] - np.mean(v)) <= bound, (int(i), k, m[0], np.mean(v), bound)
 
 
 def test_mixed_units_points():
