@@ -106,48 +106,9 @@ class _SectorEval:
         self._corner[key] = node
         return node
 
-    def inv_poly_at(self, i, W):
-        """1/P_i with t_W = 0.  When every coefficient of P_i is positive (each corner
-        value is then at least its constant term and bounded on the cube) the
-        reciprocals of all corner values of P_i are formed in batches of four with one
-        division (Montgomery's simultaneous inversion: prefix products p_k, r = 1/p_4,
-        then 1/v_k = r p_(k-1) and r <- r v_k going down), 3 multiplications per
-        further value instead of a division each; a product of four such values stays
-        well inside the binary32 range."""
-        key = ("invP", i, W)
-        if key in self._corner:
-            return self._corner[key]
-        g = self.g
-        if not all(c > 0 for c in self.sec.polys[i][0].values()):
-            self._corner[key] = g.inv(self.poly_at(i, W))
-            return self._corner[key]
-        corners = [tuple(sorted(w)) for w in _subsets(self.S)]
-        vals = []
-        for w in corners:
-            v = self.poly_at(i, w)
-            if v not in vals:
-                vals.append(v)
-        inv = {}
-        for k in range(0, len(vals), 4):
-            grp = vals[k:k + 4]
-            pre = [grp[0]]
-            for v in grp[1:]:
-                pre.append(g.mul(pre[-1], v))
-            r = g.inv(pre[-1])
-            for m in range(len(grp) - 1, 0, -1):
-                inv[grp[m]] = g.mul(r, pre[m - 1])
-                r = g.mul(r, grp[m])
-            inv[grp[0]] = r
-        for w in corners:
-            self._corner[("invP", i, w)] = inv[self.poly_at(i, w)]
-        return self._corner[key]
-
     def _pow_at(self, i, W, e):
-        """P_i^e with t_W = 0 for an integer e (negative powers from the batched reciprocal)."""
-        e = int(e)
-        if e < 0:
-            return self.g.powi(self.inv_poly_at(i, W), -e)
-        return self.g.powi(self.poly_at(i, W), e)
+        """P_i^e with t_W = 0 for an integer e."""
+        return self.g.powi(self.poly_at(i, W), int(e))
 
     def logpoly_at(self, i, W):
         key = ("logP", i, W)

@@ -237,3 +237,21 @@ def test_mixed_sector_programs_match_oracle_sums(name, group):
                     ref += o.f_numpy(X)
                     mag += P.magnitude_numpy(o, X)
             assert np.all(np.abs(Fv[:, k] - ref) <= 1e-12 * np.maximum(mag, 1e-300)), (i, k)
+
+
+def test_corner_differences_vanish_exactly_at_the_boundary():
+    """Where t_j is so small that its terms fall below half an ulp, a corner value
+    P(t_W) and P(t_W, t_j = 0) are the same number, and the subtraction difference
+    G(W) - G(W u {j}) must be exactly 0: the following 1/t_j factors would otherwise
+    amplify a rounding difference into garbage (in binary32, into inf).  So every corner
+    is evaluated by the same operation sequence; this is checked by evaluating every
+    fused double-box program in binary32 at extreme coordinates (down to 1e-30, the
+    binary32 range a flow sampler reaches, and 1 - 2^-24, 1) and requiring finite
+    values."""
+    prep = prepare_feynman(W.double_box(), fuse_orders=True)
+    vals = np.array([1e-3, 1e-8, 4.7e-15, 1e-20, 1e-30, 0.5, 1.0 - 2.0 ** -24, 1.0])
+    rng = np.random.default_rng(41)
+    for k, u in enumerate(prep.units):
+        X = rng.choice(vals, size=(400, u.dim)).astype(np.float32).astype(np.float64)
+        f = run(u.program, X, np.float32)
+        assert np.all(np.isfinite(f)), k
