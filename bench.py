@@ -345,9 +345,11 @@ def run_ours(args):
         e2e = {"value": sum_over_ranks(e_points, world) / et, "unit": "points/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
-    cpu = None
+    cpu = onp = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(prep, args.workload, 12.0)
+        units = _oracle_units(args.workload)
+        cpu = cpu_baseline(args.workload, 12.0, units)
+        onp = oracle_numpy_rate(args.workload, 6.0, units)
 
     # the metric's second part, measured live on the same GPU after the timed region:
     # GPU-seconds to 1e-4 relative error on every eps order, plain binary64 Vegas against
@@ -387,6 +389,7 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MB write)"},
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "oracle_numpy": onp,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": ck,
@@ -471,16 +474,55 @@ def _real_f(unit):
     return unit.f_numpy
 
 
-def cpu_baseline(prep_unused, workload, budget_s):
-    """The oracle as it stands, on a bounded sample of the workload, on this host's cores."""
-    import numpy as np
+def _oracle_units(workload, n_stress=200):
     import workloads as W
-    from oracle import pipeline as P, vegas as V
+    from oracle import pipeline as P
     if workload == "stress":
-        probs = W.stress_suite(200)
-        units = [P.direct_problem(p).units[0] for p in probs]
-    else:
-        units = P.feynman_problem(getattr(W, workload)(), lam=_oracle_lam(workload)).units
+        return [P.direct_problem(p).units[0] for p in W.stress_suite(n_stress)]
+    return P.feynman_problem(getattr(W, workload)(), lam=_oracle_lam(workload)).units
+
+
+def cpu_baseline(workload, budget_s, units=None):
+    """The timed CPU baseline: per-unit straight-line C++ generated from the oracle's
+    expression trees (oracle/cbaseline.py), g++ -O3 (-mcpu=native on aarch64), OpenMP
+    over units on every host core, binary64, the same Philox points and Vegas spec
+    (map, v^2 histogram, refinement), on a bounded sample of the workload's units and
+    points.  Complex (deformed-contour) units are left out: the generated code is real."""
+    import numpy as np
+    from oracle.cbaseline import Baseline, cpu_model
+    units = units if units is not None else _oracle_units(workload)
+    units = [u for u in units if not getattr(u, "complex", False)]
+    if not units:
+        return None
+    step = max(1, len(units) // 96)
+    sample = units[::step]
+    b = Baseline(sample)
+    n = 2000
+    while True:                       # calibrate: grow the sample until a pass takes >= 0.5 s
+        t0 = time.perf_counter()
+        b.iterate(n, seed=1, iteration=0)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 or n >= 1 << 22:
+            break
+        n *= 4
+    b.refine()
+    n = int(min(max(n * budget_s / max(dt, 1e-6), 4096), 1 << 24))
+    t0 = time.perf_counter()
+    b.iterate(n, seed=1, iteration=1)
+    b.refine()
+    dt = time.perf_counter() - t0
+    return {"value": n * len(sample) / dt, "unit": "points/s", "cores": b.threads, "kind": "compiled",
+            "sample": f"{len(sample)} of {len(units)} {workload} sector-order integrands (every {step}th), one "
+                      f"Vegas iteration of {n} Philox points each with refinement; C++ generated from the oracle's "
+                      f"expression trees, binary64, OpenMP over units",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(), "compile_s": b.compile_s,
+            "flags": " ".join(__import__("oracle.cbaseline", fromlist=["compile_flags"]).compile_flags())}
+
+
+def oracle_numpy_rate(workload, budget_s, units=None):
+    """The oracle as it stands (numpy float64, one thread) on a bounded sample."""
+    from oracle import vegas as V
+    units = units if units is not None else _oracle_units(workload)
     n = 20000
     done = 0
     t0 = time.perf_counter()
