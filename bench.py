@@ -64,15 +64,19 @@ def parse():
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
     ap.add_argument("--target", type=float, default=1e-4)
     ap.add_argument("--max-iters", type=int, default=400, help="tta mode: Vegas iteration cap per form")
+    ap.add_argument("--cap-s", type=float, default=0.0, help="tta mode: GPU-seconds cap per form (0: none)")
+    ap.add_argument("--small-x32", type=float, default=-1.0,
+                    help="tta mode: binary64 below this coordinate in binary32 units (-1: the binding default)")
     return ap.parse_args()
 
 
-def prepared(workload, fuse=False, mix=1):
+def prepared(workload, fuse=False, mix=1, terms=False):
     import workloads as W
     from paper_1511_03614_gb300 import prepare_feynman, prepare_direct
     if workload == "stress":
         return prepare_direct(W.stress_suite(), "stress")
-    return prepare_feynman(getattr(W, workload)(), fuse_orders=bool(fuse), mix_sectors=mix)
+    return prepare_feynman(getattr(W, workload)(), fuse_orders=bool(fuse), mix_sectors=mix,
+                           separate_terms=bool(terms))
 
 
 def dist_setup(args):
@@ -422,6 +426,8 @@ def time_to_accuracy(workload, target, cap_s=15.0):
                                                                  max_iters=400, **cap)),
                 ("rqmc_fp64", True, lambda ig: run_to_accuracy_rqmc(ig, target=target, points=1 << 18,
                                                                     max_points=1 << 22)),
+                ("rqmc_fp64_terms", "terms", lambda ig: run_to_accuracy_rqmc(ig, target=target, points=1 << 18,
+                                                                             max_points=1 << 22)),
                 ("auto_alloc", False, lambda ig: run_to_accuracy(ig, target=target, points=2_000_000,
                                                                  max_iters=400, precision="auto", allocate=True,
                                                                  **cap)),
@@ -439,7 +445,7 @@ def time_to_accuracy(workload, target, cap_s=15.0):
     for name, fuse, fn in runs:
         try:
             t0 = time.perf_counter()
-            ig = Integrator(prepared(workload, fuse=fuse))
+            ig = Integrator(prepared(workload, fuse=bool(fuse), terms=fuse == "terms"))
             r = fn(ig)
             rec = {"gpu_s": r["gpu_s"], "converged": r["converged"], "wall_s": time.perf_counter() - t0}
             if not r["converged"] and r.get("ratio"):
@@ -605,15 +611,15 @@ def run_tta(args):
         integ = Integrator(prep)
         try:
             integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
+            sx = 1e-2 if "_mixed" in form else (None if args.small_x32 < 0 else args.small_x32)
             r = run_to_accuracy(integ, target=args.target, points=pts, precision=prec, max_iters=args.max_iters,
-                                allocate=form.endswith("_alloc"),
-                                small_x32=1e-2 if "_mixed" in form else 0.0)
+                                allocate=form.endswith("_alloc"), small_x32=sx, max_gpu_s=args.cap_s or None)
         except FiestaError as e:
             out["runs"][form] = {"error": str(e)}
             integ.close()
             continue
         out["runs"][form] = {"gpu_s": r["gpu_s"], "points": r["points"], "iterations": r["iterations"],
-                             "converged": r["converged"],
+                             "converged": r["converged"], "error_over_target": r.get("ratio"),
                              "values": {str(n): [_num(r["values"][n]), _num(r["errors"][n])] for n in r["values"]}}
         integ.close()
     # learned proposal: flow sampling with training rounds, binary32 integrand
@@ -634,11 +640,13 @@ def run_tta(args):
     integ.close()
     # randomised quasi-Monte Carlo on adapted Vegas grids (Sobol replicates), fused units
     from paper_1511_03614_gb300.api import run_to_accuracy_rqmc
-    for form in ("rqmc_fp64", "rqmc_fp64_mix4"):
+    for form in ("rqmc_fp64", "rqmc_fp64_mix4", "rqmc_fp64_terms"):
         if form not in forms:
             continue
-        # *_mix4: four sectors of equal dimension summed into one program (MixSectors)
-        integ = Integrator(prepared(args.workload, fuse=True, mix=4 if form.endswith("mix4") else 1))
+        # *_mix4: four sectors of equal dimension summed into one program (MixSectors);
+        # *_terms: every separately integrable term its own unit (SeparateTerms)
+        integ = Integrator(prepared(args.workload, fuse=True, mix=4 if form.endswith("mix4") else 1,
+                                    terms=form.endswith("terms")))
         try:
             prec = form.split("_")[1]
             integ.integrate(n_iter=1, points=min(pts, 100_000), precision=prec)      # warm-up and autotuning
@@ -659,7 +667,7 @@ def run_tta(args):
         integ.cuhre(rel_tol=1e-2, max_passes=2)                                   # warm-up
         r = run_cuhre_to_accuracy(integ, target=args.target)
         out["runs"]["cuhre_fp64"] = {"gpu_s": r["gpu_s"], "points": r["points"], "rounds": r["rounds"],
-                                     "rel_tol": r["rel_tol"], "regions": r["regions"], "converged": r["converged"],
+                                     "rel_tol": r["rel_tol"], "converged": r["converged"],
                                      "values": {str(n): [_num(r["values"][n]), _num(r["errors"][n])]
                                                 for n in r["values"]}}
     except FiestaError as e:

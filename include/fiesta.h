@@ -16,8 +16,10 @@
  *  - A return value of 0 (FIESTA_OK) means success; a negative value is one of
  *    the FIESTA_E_* codes below and fiesta_last_error() returns a message
  *    (thread-local, valid until the next call on the same thread).
- *  - Nothing is computed on the host: if no usable GPU is present every entry
- *    point that would compute returns FIESTA_E_CUDA.
+ *  - Nothing of the integration is computed on the host: if no usable GPU is
+ *    present every entry point that would evaluate integrands returns
+ *    FIESTA_E_CUDA.  The accuracy loop's bookkeeping (fiesta_assemble,
+ *    fiesta_allocate_points) is plain host arithmetic on a few numbers per result.
  */
 #ifndef FIESTA_H
 #define FIESTA_H
@@ -39,9 +41,17 @@ extern "C" {
 #define FIESTA_RNG_PHILOX    0
 #define FIESTA_RNG_SOBOL     1
 #define FIESTA_FP64          0  /* all arithmetic in binary64 */
-#define FIESTA_FP32          1  /* integrand body in binary32; map, Jacobian, sums and grid in binary64 */
+#define FIESTA_FP32          1  /* integrand body and map in binary32; sums, Vegas histogram and grid in
+                                   binary64; points with a coordinate below small_x32 in binary64 */
 #define FIESTA_AUTO          2  /* per unit: binary32 where a probe against binary64 stays within budget */
 #define FIESTA_DD            3  /* fiesta_eval_batch only: every point in double-double (about 106 bits) */
+
+#define FIESTA_PROPOSAL_VEGAS 0  /* sampling points from the Vegas map of each unit */
+#define FIESTA_PROPOSAL_FLOW  1  /* sampling points from each unit's normalising flow (learned proposal) */
+
+#define FIESTA_METHOD_VEGAS  0  /* fiesta_integrate_to_accuracy: Vegas iterations (either proposal) */
+#define FIESTA_METHOD_RQMC   1  /* adapted Vegas grids, then digitally shifted Sobol replicates */
+#define FIESTA_METHOD_CUHRE  2  /* adaptive cubature with a shrinking per-unit tolerance */
 
 #define FIESTA_NBINS       128  /* Vegas bins per coordinate */
 #define FIESTA_MAX_DIM       8  /* largest integration dimension */
@@ -119,7 +129,23 @@ typedef struct {
     double small_x32;         /* the same one level down: > 0 evaluates every point of a binary32
                                  unit with a coordinate below small_x32 in binary64 (the
                                  subtraction differences near the boundary stay binary64), and the
-                                 FIESTA_AUTO probe counts such points as exact for binary32; 0 = off. */
+                                 FIESTA_AUTO probe counts such points as exact for binary32; 0 = off.
+                                 The Python binding passes 2^-20 for binary32 and AUTO: below it a
+                                 coordinate's terms fall under half a binary32 ulp of the corner
+                                 polynomials, so f(t) - f(t|t_j=0) would vanish instead of giving
+                                 its finite limit (a bias, not noise). */
+    int32_t proposal;         /* FIESTA_PROPOSAL_VEGAS (0) or FIESTA_PROPOSAL_FLOW: each iteration then
+                                 draws its points from the units' flows (fiesta_flow_*; initialised
+                                 with seed on first use), precision FIESTA_FP64 or FIESTA_FP32, Philox
+                                 points; between iterations the flows are trained flow_train_steps
+                                 Adam steps on flow_keep points per unit kept from the iteration;
+                                 iterations are combined as Vegas iterations are.  adapt, rng,
+                                 unit_points and small_x do not apply. */
+    int32_t flow_train_steps; /* FLOW: training steps after every iteration but the last (0: none) */
+    int64_t flow_keep;        /* FLOW: points kept per unit for training (0: 4096) */
+    double flow_lr;           /* FLOW: Adam learning rate (0: 2e-3) */
+    int32_t flow_power;       /* FLOW: loss weights (|f|/q)^power (0: 1, the KL divergence) */
+    int32_t reserved2;
 } fiesta_options;
 
 typedef struct {
@@ -180,6 +206,118 @@ int fiesta_load_sectors(fiesta_ctx **out, const fiesta_program *progs, int64_t n
  */
 int fiesta_integrate(fiesta_ctx *ctx, const fiesta_options *opt, double *value, double *error,
                      int32_t n_orders, fiesta_unit_result *per_unit, fiesta_stats *stats);
+
+/*
+ * Integrate until every eps order n of the assembled series R_n = sum_m c_m I_(n-m)
+ * (I_K the per-order sums over units, c the caller's prefactor series) has an error
+ * at most target * max(|R_n|, floor * max_k |R_k|) -- the accuracy loop of the
+ * paper's pool (Sec. 4.5-4.6: integrate, check the error, continue), on the device
+ * side.  Methods:
+ *  FIESTA_METHOD_VEGAS: calls of fiesta_integrate with iters_per_call iterations
+ *    (grids kept and refined between calls, iteration numbers continuing); every
+ *    iteration but the first `skip` enters a per-result inverse-variance combination;
+ *    with allocate, the points of each later call go to the units by Neyman
+ *    allocation for the assembled series (unit u's per-point spread s_uK, cost per
+ *    point w_u = program length + 4 dim + 8, N_u proportional to
+ *    sqrt(max_n (sum_K |c_(n-K)| s_uK / tau_n)^2 / w_u), total cost unchanged, each
+ *    N_u within [0.01, 64] x points).  With proposal FLOW each round draws `points`
+ *    from the flows (keeping `keep` per unit for training during the first
+ *    train_rounds rounds, then steps_per_round Adam steps); rounds from `skip` on are
+ *    combined.
+ *  FIESTA_METHOD_RQMC: adapt_iters Philox iterations adapt the grids (adapt_points
+ *    points, 0: points); then each round integrates every unit with `replicates`
+ *    independent digital shifts of a Sobol sequence of N points (N = points, doubled
+ *    every round up to max_points) on the frozen grids; a result's round estimate is
+ *    the replicate mean, its variance the replicates' sample variance / replicates;
+ *    rounds are combined with inverse-variance weights.
+ *  FIESTA_METHOD_CUHRE: fiesta_cuhre with per-unit tolerance rel_tol (0: target),
+ *    multiplied by shrink (0: 0.1) after every attempt that misses the target; errors
+ *    are bounds and add linearly.
+ * A call continues from `state` (caller-owned, zeroed for a fresh start): sw, swi
+ * (one entry per result of every unit, n_out per unit in unit order) and n_used (one
+ * per unit) are read and updated, so a caller can stop (max_calls), save the state
+ * and resume with the same point streams.  Outputs (host arrays, caller-owned):
+ * value/error per assembled order out_lo + k, k < n_out_orders (real parts and their
+ * errors; value_im/error_im, nullable, the imaginary parts of problems with complex
+ * units), unit_value/unit_sigma (nullable) per result.  The ratio max_n error/target
+ * and the converged flag are in state.  Errors: those of the calls it makes.
+ */
+typedef struct {
+    int32_t method;            /* FIESTA_METHOD_* */
+    int32_t proposal;          /* METHOD_VEGAS: FIESTA_PROPOSAL_VEGAS or FIESTA_PROPOSAL_FLOW */
+    int32_t precision;         /* FIESTA_FP64, FIESTA_FP32 or FIESTA_AUTO (flow: FP64 or FP32) */
+    int32_t allocate;          /* METHOD_VEGAS, Vegas proposal: Neyman allocation across units */
+    double target;             /* relative error per order of the assembled series, > 0 */
+    double floor;              /* order n is judged against max(|R_n|, floor * max_k |R_k|) */
+    int64_t points;            /* points per unit per iteration (RQMC: the first Sobol length) */
+    int32_t iters_per_call;    /* METHOD_VEGAS: iterations per fiesta_integrate call (0: 2) */
+    int32_t max_iters;         /* iteration (flow, RQMC: round; cubature: attempt) cap */
+    int32_t skip;              /* leading iterations (flow rounds) left out of the combination */
+    int32_t max_calls;         /* METHOD_VEGAS: return after this many calls (0: no limit) */
+    uint64_t seed;
+    double max_gpu_s;          /* return once this much device time is spent (0: no cap) */
+    double small_x, small_x32; /* as in fiesta_options */
+    const double *pre;         /* prefactor series c_i (host, n_pre values): c(eps) = sum c_i eps^(i - pre_q) */
+    int32_t n_pre;
+    int32_t pre_q;
+    int32_t correlated;        /* nonzero: the assembled errors add linearly (fused units' orders are correlated) */
+    int32_t out_lo;            /* value[k] refers to eps^(out_lo + k) */
+    int32_t replicates;        /* RQMC: digital shifts per round (0: 8) */
+    int32_t adapt_iters;       /* RQMC: Philox iterations adapting the grids (0: 6) */
+    int64_t adapt_points;      /* RQMC: points per unit of those iterations (0: points) */
+    int64_t max_points;        /* RQMC: largest Sobol length per replicate (0: 2^22) */
+    int32_t train_rounds;      /* FLOW: rounds with training (0: 8) */
+    int32_t steps_per_round;   /* FLOW: Adam steps per training round (0: 20) */
+    double lr;                 /* FLOW: learning rate (0: 2e-3) */
+    int32_t power;             /* FLOW: loss weight exponent (0: 1) */
+    int32_t reserved;
+    int64_t keep;              /* FLOW: points kept per unit for training (0: 4096) */
+    double rel_tol;            /* CUHRE: first per-unit tolerance (0: target) */
+    double shrink;             /* CUHRE: tolerance factor per missed attempt (0: 0.1) */
+    int32_t max_passes;        /* CUHRE: passes per attempt (0: 60) */
+    int32_t reserved2;
+    int64_t max_regions;       /* CUHRE: region limit per attempt (0: 2^22) */
+} fiesta_accuracy_options;
+
+typedef struct {
+    double *sw, *swi;          /* per result: running sums of 1/var and mean/var (caller-owned) */
+    double *n_used;            /* per unit: points counted so far (caller-owned) */
+    int32_t iterations;        /* iterations, rounds or attempts done */
+    int32_t converged;         /* every order met its target */
+    double gpu_ms;             /* device time of all calls so far */
+    int64_t points;            /* (sector, order) integrand evaluations so far */
+    double ratio;              /* max over orders of |error| / target after the last check */
+    int64_t points_per_replicate; /* RQMC: the last Sobol length */
+    double rel_tol;            /* CUHRE: the last per-unit tolerance */
+} fiesta_accuracy_state;
+
+int fiesta_integrate_to_accuracy(fiesta_ctx *ctx, const fiesta_accuracy_options *opt, fiesta_accuracy_state *state,
+                                 int32_t n_out_orders, double *value, double *error, double *value_im,
+                                 double *error_im, double *unit_value, double *unit_sigma);
+
+/*
+ * The two arithmetic steps of that loop as plain host functions (no GPU, no
+ * context), used by it and exposed so that they can be checked on their own.
+ * fiesta_assemble: per-order sums of n_rec results (eps order order[k], part[k] 0
+ *   real / 1 imaginary, value val[k], error sig[k]) -- errors in the mean-square norm
+ *   (Sec. 4.3), or added when `linear` (error bounds) -- then the prefactor series of
+ *   opt (pre, n_pre, pre_q, correlated, out_lo): value/error (and value_im/error_im,
+ *   nullable) for the assembled orders out_lo .. out_lo + n_out - 1; *ratio
+ *   (nullable) = max_n |error_n| / (target * max(|R_n|, floor * max_k |R_k|)).
+ * fiesta_allocate_points: the Neyman allocation of the loop above for n_units units
+ *   of cost cost[u] per point (program length + 4 dim + 8 in the loop), from the
+ *   results' errors sig[k] (rec_unit[k], rec_order[k]), the points each unit has used
+ *   (n_used) and the assembled values (value, value_im nullable: n_out orders from
+ *   out_lo) that set the targets; points[u] receives the allocation.
+ * Errors: FIESTA_E_INVALID.
+ */
+int fiesta_assemble(const fiesta_accuracy_options *opt, int64_t n_rec, const int32_t *order, const int32_t *part,
+                    const double *val, const double *sig, int32_t linear, int32_t n_out, double *value,
+                    double *error, double *value_im, double *error_im, double *ratio);
+int fiesta_allocate_points(const fiesta_accuracy_options *opt, int64_t n_units, const double *cost, int64_t n_rec,
+                           const int64_t *rec_unit, const int32_t *rec_order, const double *sig,
+                           const double *n_used, int32_t n_out, const double *value, const double *value_im,
+                           int64_t *points);
 
 /*
  * Evaluate unit `unit` at n points: x is n*dim coordinates in (0,1), row-major,

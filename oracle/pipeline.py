@@ -9,6 +9,7 @@ multiplied in (Eq. 2).
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 
 import numpy as np
@@ -27,6 +28,7 @@ class Unit:
     variables: tuple            # original indices; dimension i of the cube <-> variables[i]
     expr: object                # sympy expression in t-symbols
     complex: bool = False       # deformed contour: complex values
+    term: tuple = None          # separately integrable term: the variables whose pole term it is
     _np: object = None
     _mp: object = None
 
@@ -66,10 +68,27 @@ class Problem:
     out_orders: tuple         # orders n of the final result
 
 
-def feynman_problem(problem, strategy="M", lam=None):
+def _term_units(i, s, K):
+    """The separately integrable terms of unit (sector i, order K): one unit per subset
+    T of the singular variables, over the variables not in T (the term is constant
+    along those; a term over no variable keeps the first one)."""
+    units = []
+    Sv = S.singular_vars(s)
+    for r in range(len(Sv) + 1):
+        for T in itertools.combinations(Sv, r):
+            e = S.unit_integrand(s, K, term=T)
+            if e == 0:
+                continue
+            var = tuple(j for j in s.variables if j not in T) or (s.variables[0],)
+            units.append(Unit(i, K, var, e, term=tuple(T)))
+    return units
+
+
+def feynman_problem(problem, strategy="M", lam=None, separate_terms=False):
     """Units of a Feynman integral.  ``lam``: a contour-deformation parameter per
     sector (callable sector -> lam or None, or one number for every sector whose F
-    has a coefficient that is not positive)."""
+    has a coefficient that is not positive).  ``separate_terms``: one unit per
+    separately integrable term of every real sector and order (``_term_units``)."""
     U, F, xs = symanzik(problem)
     L = len(problem.loop_momenta)
     prim = S.primary_sectors(U, F, xs, problem.indices, L)
@@ -87,6 +106,9 @@ def feynman_problem(problem, strategy="M", lam=None):
         else:
             ls = None
         for K in range(max(kmin, S.min_order(s)), khi + 1):
+            if separate_terms and ls is None:
+                units += _term_units(i, s, K)
+                continue
             e = S.unit_integrand(s, K, ls)
             if e != 0:
                 units.append(Unit(i, K, s.variables, e, complex=ls is not None))

@@ -246,11 +246,15 @@ def deformation(sec: Sector, lam, poly_index=-1):
     return z, w, sp.expand(J.det())
 
 
-def unit_integrand(sec: Sector, K: int, lam=None):
+def unit_integrand(sec: Sector, K: int, lam=None, term=None):
     """The sympy expression of the eps^K coefficient of the subtracted sector integrand.
 
     Variables not integrated analytically keep their t-dependence; variables whose
     pole term was taken appear not at all (the integrand is constant along them).
+    The expression is a sum over the subsets T of the singular variables whose pole
+    term is taken; each such term is integrable on its own (the paper's SeparateTerms
+    option, Sec. 4.4, hands them to the integrator one by one): ``term`` = T (a tuple
+    of variables, a subset of ``singular_vars``) keeps that term only.
     With ``lam`` the contour is deformed (``deformation``): the integrand
     prod_j z_j^{c_j + b_j eps} G(z) det J equals prod_j t_j^{c_j + b_j eps} times
     [prod_j w_j^{c_j + b_j eps} G(z) det J], and the bracket takes the place of G
@@ -259,6 +263,7 @@ def unit_integrand(sec: Sector, K: int, lam=None):
     S = singular_vars(sec)
     if K < -len(S):
         return sp.Integer(0)
+    wanted = None if term is None else tuple(sorted(term))
     t = {j: tsym(j) for j in sec.variables}
     # G_n = prod P^{a0} * extra logs * L^n / n!,  L = sum a1 log P
     G0 = sp.Integer(1)
@@ -290,6 +295,8 @@ def unit_integrand(sec: Sector, K: int, lam=None):
     total = sp.Integer(0)
     for r in range(len(S) + 1):
         for T in itertools.combinations(S, r):
+            if wanted is not None and tuple(sorted(T)) != wanted:
+                continue
             rest = [j for j in S if j not in T]
             ptuples = [range(-sec.mono[j][0]) for j in T]   # k = 0..p_j  (p_j = -1 - c_j)
             for ks in itertools.product(*ptuples):

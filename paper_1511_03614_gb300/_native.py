@@ -10,6 +10,8 @@ FIESTA_OK = 0
 ERRORS = {-1: "FIESTA_E_INVALID", -2: "FIESTA_E_NOMEM", -3: "FIESTA_E_CUDA",
           -4: "FIESTA_E_TIMEOUT", -5: "FIESTA_E_NONFINITE"}
 RNG = {"philox": 0, "sobol": 1}
+PROPOSAL = {"vegas": 0, "flow": 1}
+METHOD = {"vegas": 0, "rqmc": 1, "cuhre": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "auto": 2, "dd": 3}
 NBINS = 128
 MAX_DIM = 8
@@ -39,7 +41,29 @@ class Options(C.Structure):
                 ("reset_grid", C.c_int32), ("iter_offset", C.c_int32), ("points_per_thread", C.c_int32),
                 ("probe_points", C.c_int64), ("fp32_budget", C.c_double), ("no_graph", C.c_int32),
                 ("accumulate", C.c_int32), ("small_x", C.c_double),
-                ("unit_points", C.POINTER(C.c_int64)), ("small_x32", C.c_double)]
+                ("unit_points", C.POINTER(C.c_int64)), ("small_x32", C.c_double), ("proposal", C.c_int32),
+                ("flow_train_steps", C.c_int32), ("flow_keep", C.c_int64), ("flow_lr", C.c_double),
+                ("flow_power", C.c_int32), ("reserved2", C.c_int32)]
+
+
+class AccuracyOptions(C.Structure):
+    _fields_ = [("method", C.c_int32), ("proposal", C.c_int32), ("precision", C.c_int32), ("allocate", C.c_int32),
+                ("target", C.c_double), ("floor", C.c_double), ("points", C.c_int64),
+                ("iters_per_call", C.c_int32), ("max_iters", C.c_int32), ("skip", C.c_int32),
+                ("max_calls", C.c_int32), ("seed", C.c_uint64), ("max_gpu_s", C.c_double),
+                ("small_x", C.c_double), ("small_x32", C.c_double), ("pre", C.POINTER(C.c_double)),
+                ("n_pre", C.c_int32), ("pre_q", C.c_int32), ("correlated", C.c_int32), ("out_lo", C.c_int32),
+                ("replicates", C.c_int32), ("adapt_iters", C.c_int32), ("adapt_points", C.c_int64),
+                ("max_points", C.c_int64), ("train_rounds", C.c_int32), ("steps_per_round", C.c_int32),
+                ("lr", C.c_double), ("power", C.c_int32), ("reserved", C.c_int32), ("keep", C.c_int64),
+                ("rel_tol", C.c_double), ("shrink", C.c_double), ("max_passes", C.c_int32),
+                ("reserved2", C.c_int32), ("max_regions", C.c_int64)]
+
+
+class AccuracyState(C.Structure):
+    _fields_ = [("sw", C.POINTER(C.c_double)), ("swi", C.POINTER(C.c_double)), ("n_used", C.POINTER(C.c_double)),
+                ("iterations", C.c_int32), ("converged", C.c_int32), ("gpu_ms", C.c_double), ("points", C.c_int64),
+                ("ratio", C.c_double), ("points_per_replicate", C.c_int64), ("rel_tol", C.c_double)]
 
 
 class UnitResult(C.Structure):
@@ -73,6 +97,18 @@ EXPORTS = {
                                       C.c_void_p]),
     "fiesta_integrate": (C.c_int, [C.c_void_p, C.POINTER(Options), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.c_int32, C.POINTER(UnitResult), C.POINTER(Stats)]),
+    "fiesta_integrate_to_accuracy": (C.c_int, [C.c_void_p, C.POINTER(AccuracyOptions), C.POINTER(AccuracyState),
+                                               C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                               C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                               C.POINTER(C.c_double)]),
+    "fiesta_assemble": (C.c_int, [C.POINTER(AccuracyOptions), C.c_int64, C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32,
+                                  C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "fiesta_allocate_points": (C.c_int, [C.POINTER(AccuracyOptions), C.c_int64, C.POINTER(C.c_double), C.c_int64,
+                                         C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "fiesta_eval_batch": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]),
     "fiesta_iterations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),

@@ -12,7 +12,6 @@ import math
 import numpy as np
 
 from . import _native as N
-from .preprocess import assemble
 
 
 @dataclasses.dataclass
@@ -34,28 +33,43 @@ def _record_key(u, o):
     return (u.order + o // 2, o & 1) if u.cplx else (u.order + o, 0)
 
 
-def _sum_parts(records):
-    """Sums over units per eps order of (order, part, value, sigma) records: complex
-    values, and errors complex(sigma_re, sigma_im) each combined in the mean-square norm."""
-    v, e = {}, {}
-    for K, part, val, sig in records:
-        v.setdefault(K, [0.0, 0.0])[part] += val
-        e.setdefault(K, [0.0, 0.0])[part] += sig * sig
-    return ({K: complex(*x) for K, x in v.items()},
-            {K: complex(math.sqrt(x[0]), math.sqrt(x[1])) for K, x in e.items()})
+def assemble_records(prep, orders, parts, vals, sigs, linear=False, prefactor=True):
+    """fiesta_assemble on per-result records: the per-order sums (errors in the
+    mean-square norm, or added when ``linear``) and, with ``prefactor``, the eps series
+    of ``prep``; complex values for problems with complex units.  Returns (values,
+    errors) dicts keyed by eps order.  Marshalling only: the sums run in the library."""
+    lib = N.load()
+    if prefactor:
+        out_orders = tuple(prep.out_orders)
+        opts, keep = accuracy_options(prep, points=2)
+    else:
+        out_orders = tuple(range(min(orders), max(orders) + 1))
+        opts, keep = accuracy_options(prep, points=2)
+        one = np.ones(1)
+        keep = (keep, one)
+        opts.pre, opts.n_pre, opts.pre_q, opts.correlated = one.ctypes.data_as(C.POINTER(C.c_double)), 1, 0, 0
+        opts.out_lo = out_orders[0]
+    n = len(out_orders)
+    o = np.ascontiguousarray(orders, dtype=np.int32)
+    p = np.ascontiguousarray(parts, dtype=np.int32)
+    v = np.ascontiguousarray(vals, dtype=np.float64)
+    s = np.ascontiguousarray(sigs, dtype=np.float64)
+    val, err, vim, eim = (np.zeros(n) for _ in range(4))
+    dp = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+    ip = lambda x: x.ctypes.data_as(C.POINTER(C.c_int32))
+    N.check(lib.fiesta_assemble(C.byref(opts), len(v), ip(o), ip(p), dp(v), dp(s), int(bool(linear)), n, dp(val),
+                                dp(err), dp(vim), dp(eim), None))
+    if prep.complex:
+        return ({m: complex(val[i], vim[i]) for i, m in enumerate(out_orders)},
+                {m: complex(err[i], eim[i]) for i, m in enumerate(out_orders)})
+    return ({m: float(val[i]) for i, m in enumerate(out_orders)}, {m: float(err[i]) for i, m in enumerate(out_orders)})
 
 
-def _assembled(prep, recs, val, sig):
-    """Per-order sums of (unit, result) records with values ``val`` and standard errors
-    ``sig`` (mean-square combination, Sec. 4.3), then the prefactor series: complex
-    values for a problem with complex units.  Returns (assembled, errors, per-order sums)."""
-    values, errors = _sum_parts([_record_key(prep.units[unit], o) + (val[k], sig[k])
-                                 for k, (unit, o) in enumerate(recs)])
-    if not prep.complex:
-        values = {K: z.real for K, z in values.items()}
-        errors = {K: z.real for K, z in errors.items()}
-    R, E = assemble(prep, values, errors)
-    return R, E, values
+# Binary32 and AUTO units evaluate points with a coordinate below 2^-20 in binary64: below
+# it a coordinate's terms fall under half a binary32 ulp of the corner polynomials and the
+# pole-subtraction differences f(t) - f(t|t_j = 0) would vanish instead of reaching their
+# finite limit.
+SMALL_X32_DEFAULT = 2.0 ** -20
 
 
 class Integrator:
@@ -111,18 +125,21 @@ class Integrator:
     def integrate(self, n_iter=10, points=100_000, seed=1, rng="philox", precision="fp64", adapt=True,
                   alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
                   iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
-                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0, unit_points=None, small_x32=0.0,
-                  accumulate="auto"):
+                  probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0, unit_points=None, small_x32=None,
+                  accumulate="auto", proposal="vegas", flow_train_steps=0, flow_keep=0, flow_lr=0.0, flow_power=0):
         lo = min(u.order for u in self.prep.units)
         hi = max(u.order + _n_orders(u) - 1 for u in self.prep.units)
         nord = hi - lo + 1
         b, e = (0, len(self.prep.units)) if units is None else units
+        if small_x32 is None:
+            small_x32 = SMALL_X32_DEFAULT if precision in ("fp32", "auto") else 0.0
         opt = N.Options(N.RNG[rng], N.PRECISION[precision], int(n_iter), int(adapt), int(points),
                         int(seed) & 0xFFFFFFFFFFFFFFFF, float(alpha), int(bool(skip_first)), lo, int(b), int(e),
                         int(timeout_ms), int(threads), int(bool(reset_grid)), int(iter_offset),
                         int(points_per_thread), int(probe_points), float(fp32_budget), int(not graph),
                         {"auto": 0, "registers": 1, "shared": 2}[accumulate],
-                        float(small_x), None, float(small_x32))
+                        float(small_x), None, float(small_x32), N.PROPOSAL[proposal], int(flow_train_steps),
+                        int(flow_keep), float(flow_lr), int(flow_power), 0)
         if unit_points is not None:
             upts = np.ascontiguousarray(unit_points, dtype=np.int64)
             if upts.shape != (e - b,):
@@ -139,8 +156,9 @@ class Integrator:
         pu = [dict(value=r.value, sigma=r.sigma, chi2_dof=r.chi2_dof, n_points=r.n_points, order=r.order,
                    sector=r.sector, n_nonfinite=r.n_nonfinite, precision=("fp64", "fp32")[r.precision],
                    unit=r.unit, fp32_error=r.fp32_error, part=r.part) for r in per]
+        recs = ([d["order"] for d in pu], [d["part"] for d in pu], [d["value"] for d in pu], [d["sigma"] for d in pu])
         if self.prep.complex:
-            values, errors = _sum_parts([(d["order"], d["part"], d["value"], d["sigma"]) for d in pu])
+            values, errors = assemble_records(self.prep, *recs, prefactor=False)
         else:
             values = {lo + k: val[k] for k in range(nord)}
             errors = {lo + k: err[k] for k in range(nord)}
@@ -150,7 +168,7 @@ class Integrator:
                      points_per_thread=tuple(st.points_per_thread), points_ext=st.points_ext)
         res = Result(values, errors, pu, stats)
         if assemble_result and units is None:
-            res.assembled, res.assembled_errors = assemble(self.prep, values, errors)
+            res.assembled, res.assembled_errors = assemble_records(self.prep, *recs)
         return res
 
     # ------------------------------------------------------------------ cubature
@@ -175,13 +193,9 @@ class Integrator:
         pu = [dict(value=r.value, error=r.error, n_regions=r.n_regions, n_points=r.n_points, order=r.order,
                    sector=r.sector, unit=r.unit, part=r.part, converged=bool(r.converged), passes=r.passes)
               for r in per]
+        recs = ([d["order"] for d in pu], [d["part"] for d in pu], [d["value"] for d in pu], [d["error"] for d in pu])
         if self.prep.complex:
-            values, errors = {}, {}
-            for d in pu:
-                values.setdefault(d["order"], [0.0, 0.0])[d["part"]] += d["value"]
-                errors.setdefault(d["order"], [0.0, 0.0])[d["part"]] += d["error"]
-            values = {K: complex(*x) for K, x in values.items()}
-            errors = {K: complex(*x) for K, x in errors.items()}
+            values, errors = assemble_records(self.prep, *recs, linear=True, prefactor=False)
         else:
             values = {lo + k: val[k] for k in range(nord)}
             errors = {lo + k: err[k] for k in range(nord)}
@@ -190,7 +204,7 @@ class Integrator:
                      unit_points=st.unit_points)
         res = Result(values, errors, pu, stats)
         if assemble_result and units is None:
-            res.assembled, res.assembled_errors = assemble(self.prep, values, errors, correlated=True)
+            res.assembled, res.assembled_errors = assemble_records(self.prep, *recs, linear=True)
         return res
 
     def cuhre_regions(self, unit, cap=1 << 20):
@@ -407,237 +421,177 @@ def load_checkpoint(path, integ=None):
     return state
 
 
-def allocate_points(prep, sig, n_used, values, target, floor, points, lo_frac=0.01, hi_mult=64):
-    """Points per unit for the next iterations: Neyman allocation for the assembled
-    series.  Unit u's per-point standard deviation of its eps-order-K integral is
-    s_uK = sigma_uK sqrt(points used so far); its share of the error of result order n
-    is sum_K |c_(n-K)| s_uK / sqrt(N_u) (c the prefactor series); with
-    B_u = max_n (sum_K |c_(n-K)| s_uK / tau_n)^2 and a cost per point w_u (program
-    length + map), N_u proportional to sqrt(B_u / w_u) minimises the cost at a given
-    error.  The total cost equals that of ``points`` per unit; each N_u is clamped to
-    [lo_frac * points, hi_mult * points]."""
+def _records(prep):
+    """(unit, result) of every record, in the library's order (n_out per unit)."""
+    return [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
+
+
+def accuracy_options(prep, method="vegas", proposal="vegas", target=1e-4, floor=1e-2, points=1_000_000,
+                     precision="fp64", allocate=False, iters_per_call=2, max_iters=200, skip=1, max_calls=0, seed=1,
+                     max_gpu_s=0.0, small_x=0.0, small_x32=None, replicates=8, adapt_iters=6, adapt_points=0,
+                     max_points=1 << 22, train_rounds=8, steps_per_round=20, lr=2e-3, power=1, keep=4096,
+                     rel_tol=0.0, shrink=0.1, max_passes=60, max_regions=1 << 22):
+    """fiesta_accuracy_options for a Prepared problem (its prefactor series, its assembled
+    orders, correlated errors for fused units) -- marshalling only."""
     q, coeffs = prep.prefactor
-    R = assemble(prep, values, {K: 0.0 for K in values})[0]
-    big = max(abs(v) for v in R.values())
-    tau = {n: target * max(abs(R[n]), floor * big) for n in R}
-    s = {}
-    k = 0
-    for ui, u in enumerate(prep.units):
-        for o in range(u.n_out):
-            K, part = _record_key(u, o)
-            s.setdefault(ui, {}).setdefault(K, 0.0)
-            s[ui][K] += (sig[k] ** 2) * n_used[ui]
-            k += 1
-    cost = np.array([len(u.program.code) + 4 * u.dim + 8 for u in prep.units], dtype=float)
-    B = np.zeros(len(prep.units))
-    for ui in range(len(prep.units)):
-        for n, t in tau.items():
-            acc = 0.0
-            for K, s2 in s[ui].items():
-                i = n - K + q
-                if 0 <= i < len(coeffs):
-                    acc += abs(float(coeffs[i])) * math.sqrt(s2)
-            B[ui] = max(B[ui], (acc / t) ** 2)
-    wgt = np.sqrt(np.maximum(B, 0.0) / cost)
-    if not np.any(wgt > 0):
-        return np.full(len(prep.units), int(points), dtype=np.int64)
-    N = wgt * (points * cost.sum()) / float(np.sum(wgt * cost))
-    N = np.clip(N, max(2, lo_frac * points), hi_mult * points)
-    return np.maximum(N.astype(np.int64), 2)
+    pre = np.ascontiguousarray([float(c) for c in coeffs], dtype=np.float64)
+    if small_x32 is None:
+        small_x32 = SMALL_X32_DEFAULT if precision in ("fp32", "auto") else 0.0
+    o = N.AccuracyOptions()
+    o.method, o.proposal, o.precision = N.METHOD[method], N.PROPOSAL[proposal], N.PRECISION[precision]
+    o.allocate, o.target, o.floor, o.points = int(bool(allocate)), float(target), float(floor), int(points)
+    o.iters_per_call, o.max_iters, o.skip, o.max_calls = int(iters_per_call), int(max_iters), int(skip), int(max_calls)
+    o.seed, o.max_gpu_s = int(seed) & 0xFFFFFFFFFFFFFFFF, float(max_gpu_s or 0.0)
+    o.small_x, o.small_x32 = float(small_x), float(small_x32)
+    o.pre, o.n_pre, o.pre_q = pre.ctypes.data_as(C.POINTER(C.c_double)), len(pre), int(q)
+    o.correlated = int(any(_n_orders(u) > 1 for u in prep.units))
+    o.out_lo = int(min(prep.out_orders))
+    o.replicates, o.adapt_iters, o.adapt_points, o.max_points = (int(replicates), int(adapt_iters),
+                                                                 int(adapt_points or 0), int(max_points))
+    o.train_rounds, o.steps_per_round, o.lr, o.power, o.keep = (int(train_rounds), int(steps_per_round), float(lr),
+                                                                 int(power), int(keep))
+    o.rel_tol, o.shrink, o.max_passes, o.max_regions = float(rel_tol), float(shrink), int(max_passes), int(max_regions)
+    return o, pre
+
+
+def new_accuracy_state(prep):
+    """Zeroed running sums for fiesta_integrate_to_accuracy (numpy arrays + the struct)."""
+    nrec = sum(u.n_out for u in prep.units)
+    arrays = dict(sw=np.zeros(nrec), swi=np.zeros(nrec), n_used=np.zeros(len(prep.units)))
+    st = N.AccuracyState()
+    for k, v in arrays.items():
+        setattr(st, k, v.ctypes.data_as(C.POINTER(C.c_double)))
+    return st, arrays
+
+
+def integrate_to_accuracy(integ, state=None, **kw):
+    """One call of fiesta_integrate_to_accuracy on ``integ``'s units; ``state`` (from
+    new_accuracy_state, or None for a fresh start) continues across calls.  Returns the
+    result dict (assembled values and errors per order, complex where the problem has
+    complex units; per-record values and sigmas; device seconds, points, iterations,
+    converged, ratio) and the state."""
+    prep = integ.prep
+    opts, keep_alive = accuracy_options(prep, **kw)
+    st, arrays = state if state is not None else new_accuracy_state(prep)
+    orders = tuple(prep.out_orders)
+    n = len(orders)
+    nrec = sum(u.n_out for u in prep.units)
+    val, err, vim, eim = (np.zeros(n) for _ in range(4))
+    uv, us = np.zeros(nrec), np.zeros(nrec)
+    dp = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+    with integ._torch.cuda.device(integ.device):
+        N.check(integ.lib.fiesta_integrate_to_accuracy(integ.ctx, C.byref(opts), C.byref(st), n, dp(val), dp(err),
+                                                       dp(vim), dp(eim), dp(uv), dp(us)))
+    if prep.complex:
+        values = {m: complex(val[i], vim[i]) for i, m in enumerate(orders)}
+        errors = {m: complex(err[i], eim[i]) for i, m in enumerate(orders)}
+    else:
+        values = {m: float(val[i]) for i, m in enumerate(orders)}
+        errors = {m: float(err[i]) for i, m in enumerate(orders)}
+    res = dict(gpu_s=st.gpu_ms * 1e-3, points=st.points, iterations=st.iterations, values=values, errors=errors,
+               converged=bool(st.converged), ratio=st.ratio, unit_values=uv, unit_sigmas=us,
+               points_per_replicate=st.points_per_replicate, rel_tol=st.rel_tol)
+    return res, (st, arrays)
 
 
 def run_to_accuracy(integ, target=1e-4, points=1_000_000, iters_per_call=2, max_iters=200, seed=1,
-                    precision="fp64", rng="philox", floor=1e-2, skip_first=1, checkpoint=None, resume=None,
-                    stop_after=None, allocate=False, small_x=0.0, small_x32=0.0, max_gpu_s=None):
-    """Vegas until every eps order of the assembled result has sigma <= target * max(|R|, floor * max|R|).
-
-    Iterations are combined per unit with inverse-variance weights across calls
-    (the first ``skip_first`` iterations, spent adapting the grid, are left out),
-    units are summed per order with mean-square errors (Sec. 4.3 of the paper)
-    and the prefactor series is multiplied in.  ``checkpoint`` writes the state
-    after every call; ``resume`` continues from such a file with the same point
-    streams (iteration numbers continue); ``stop_after`` ends after that many
-    iterations (to emulate an interrupted job).  Returns a dict with the GPU
-    seconds (the library's device time over all calls), the points, the
-    iterations and the final values and errors.  ``allocate`` spends the points of
-    every call after the first where the variance is (``allocate_points``) instead of
-    evenly; the total points per iteration stay nu * points.  ``small_x`` /
-    ``small_x32`` promote points near the boundary of binary64 / binary32 units one
-    precision level (see fiesta_options).  ``max_gpu_s`` stops once that much device
-    time is spent; ``ratio`` in the result is max over orders of error / target.
-    """
-    prep = integ.prep
-    recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
-    unit_pts = None
-    n_used = np.zeros(len(prep.units))
-    nu = len(recs)
-    sw = np.zeros(nu)
-    swi = np.zeros(nu)
-    gpu_ms = 0.0
-    points_done = 0
-    it = 0
-    res = None
+                    precision="fp64", floor=1e-2, skip_first=1, checkpoint=None, resume=None,
+                    stop_after=None, allocate=False, small_x=0.0, small_x32=None, max_gpu_s=None):
+    """Vegas until every eps order of the assembled result has sigma <= target * max(|R|,
+    floor * max|R|): fiesta_integrate_to_accuracy with FIESTA_METHOD_VEGAS (iterations
+    combined per result across calls, the first ``skip_first`` left out; ``allocate``:
+    Neyman allocation of the points across units).  ``checkpoint`` writes the state
+    after every call, ``resume`` continues from such a file with the same point streams,
+    ``stop_after`` ends after that many iterations (an interrupted job): then the library
+    is called one fiesta_integrate call at a time and the file is written in between."""
+    kw = dict(method="vegas", target=target, floor=floor, points=points, precision=precision, allocate=allocate,
+              iters_per_call=iters_per_call, max_iters=max_iters, skip=skip_first, seed=seed,
+              max_gpu_s=max_gpu_s or 0.0, small_x=small_x, small_x32=small_x32)
+    state = new_accuracy_state(integ.prep)
     if resume is not None:
-        st = load_checkpoint(resume, integ)
-        sw, swi, it = st["sw"], st["swi"], st["it"]
-        gpu_ms, points_done, seed = st["gpu_ms"], st["points_done"], st["seed"]
-    while it < max_iters:
-        r = integ.integrate(n_iter=iters_per_call, points=points, seed=seed, rng=rng, precision=precision,
-                            adapt=2, reset_grid=(it == 0), iter_offset=it, assemble_result=False,
-                            unit_points=unit_pts, small_x=small_x, small_x32=small_x32)
-        gpu_ms += r.stats["gpu_ms"]
-        points_done += r.stats["unit_points"]
-        used_now = np.full(len(prep.units), float(points)) if unit_pts is None else unit_pts.astype(float)
-        n_used += used_now * sum(1 for j in range(iters_per_call) if it + j >= skip_first)
-        for k, (unit, o) in enumerate(recs):
-            m, v = integ.iterations(unit, iters_per_call, o)
-            for j in range(iters_per_call):
-                if it + j < skip_first:
-                    continue
-                w = 1.0 / v[j] if v[j] > 0 else 1e300
-                sw[k] += w
-                swi[k] += w * m[j]
-        it += iters_per_call
+        ck = load_checkpoint(resume, integ)
+        st, arrays = state
+        arrays["sw"][:], arrays["swi"][:] = ck["sw"], ck["swi"]
+        st.iterations, st.gpu_ms, st.points = ck["it"], ck["gpu_ms"], ck["points_done"]
+        kw["seed"] = ck["seed"]
+    step = checkpoint is not None or stop_after is not None
+    while True:
+        res, state = integrate_to_accuracy(integ, state, max_calls=1 if step else 0, **kw)
+        st, arrays = state
         if checkpoint is not None:
-            save_checkpoint(checkpoint, integ, dict(it=it, seed=seed, precision=precision, rng=rng, points=points,
-                                                    gpu_ms=gpu_ms, points_done=points_done, sw=sw, swi=swi))
-        if it <= skip_first:
-            continue
-        val = swi / sw
-        sig = np.sqrt(1.0 / sw)
-        R, E, values = _assembled(prep, recs, val, sig)
-        big = max(abs(v) for v in R.values())
-        ratio = _worst_ratio(R, E, target, floor)
-        ok = ratio <= 1.0
-        res = dict(gpu_s=gpu_ms * 1e-3, points=points_done, iterations=it, values=R, errors=E, converged=ok,
-                   unit_values=val.copy(), unit_sigmas=sig.copy(), ratio=ratio)
-        if ok or (stop_after is not None and it >= stop_after) or (max_gpu_s and gpu_ms * 1e-3 >= max_gpu_s):
-            break
-        if allocate and np.all(n_used > 0):
-            unit_pts = allocate_points(prep, sig, n_used, values, target, floor, points)
-    return res
-
-
-def _worst_ratio(R, E, target, floor):
-    """max over eps orders n of |error_n| / (target * max(|R_n|, floor * max_k |R_k|))."""
-    big = max(abs(v) for v in R.values())
-    return max(abs(E[n]) / (target * max(abs(R[n]), floor * big)) for n in R)
+            save_checkpoint(checkpoint, integ, dict(it=st.iterations, seed=kw["seed"], precision=precision,
+                                                    rng="philox", points=points, gpu_ms=st.gpu_ms,
+                                                    points_done=st.points, sw=arrays["sw"], swi=arrays["swi"]))
+        if (not step or res["converged"] or st.iterations >= max_iters or
+                (stop_after is not None and st.iterations >= stop_after) or
+                (max_gpu_s and st.gpu_ms * 1e-3 >= max_gpu_s)):
+            return res
 
 
 def run_cuhre_to_accuracy(integ, target=1e-4, floor=1e-2, rel_tol=None, shrink=0.1, max_rounds=6, max_passes=60,
                           max_regions=1 << 22):
-    """Adaptive cubature until every eps order of the assembled result has an error
-    bound <= target * max(|R|, floor * max|R|) (the rule of run_to_accuracy with the
-    cubature's linear error bound in place of sigma).  The per-unit relative
-    tolerance starts at ``rel_tol`` (default: target) and shrinks by ``shrink``
-    while the assembled bound misses the target (sector contributions can cancel);
-    GPU seconds add up over all attempts."""
-    tol = target if rel_tol is None else rel_tol
-    gpu_ms, pts, res = 0.0, 0, None
-    for k in range(max_rounds):
-        r = integ.cuhre(rel_tol=tol, max_passes=max_passes, max_regions=max_regions)
-        gpu_ms += r.stats["gpu_ms"]
-        pts += r.stats["points"]
-        R, E = r.assembled, r.assembled_errors
-        big = max(abs(v) for v in R.values())
-        ok = all(abs(E[n]) <= target * max(abs(R[n]), floor * big) for n in R)
-        res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=k + 1, rel_tol=tol, values=R, errors=E, converged=ok,
-                   regions=sum(d["n_regions"] for d in r.per_unit))
-        if ok:
-            break
-        tol *= shrink
+    """Adaptive cubature until every eps order meets the target with its error bound
+    (FIESTA_METHOD_CUHRE: the per-unit tolerance starts at ``rel_tol``, default the
+    target, and shrinks by ``shrink`` after every attempt that misses)."""
+    res, _ = integrate_to_accuracy(integ, method="cuhre", target=target, floor=floor, rel_tol=rel_tol or 0.0,
+                                   shrink=shrink, max_iters=max_rounds, max_passes=max_passes,
+                                   max_regions=max_regions, points=2)
+    res["rounds"] = res["iterations"]
     return res
 
 
 def run_to_accuracy_rqmc(integ, target=1e-4, points=1 << 18, replicates=8, adapt_iters=6, adapt_points=None,
-                         max_rounds=12, seed=1, precision="fp64", floor=1e-2, max_points=1 << 24):
-    """Randomised quasi-Monte Carlo on Vegas grids.  The grids are first adapted with
-    ``adapt_iters`` Philox iterations; then each round integrates every unit with
-    ``replicates`` independent digital shifts of a Sobol sequence of N points on the
-    frozen grids (one iteration each, no adaptation).  The replicate means are
-    independent unbiased estimates, so a unit's estimate is their average and its
-    error their standard deviation over sqrt(replicates) (no variance formula for
-    correlated points is needed).  N doubles every round (Sobol points come in powers
-    of two) until every eps order meets the target (the rule of run_to_accuracy);
-    rounds are combined with inverse-variance weights; the sequence stops growing at
-    ``max_points`` per replicate.  Binary64 is the intended precision: binary32
-    rounding near the boundary adds point-wise noise that the replicate spread does
-    not average like the quadrature error.  Returns what run_to_accuracy returns, with
-    ``rounds`` and ``points_per_replicate``."""
-    prep = integ.prep
-    recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
-    gpu_ms, pts = 0.0, 0
-    r = integ.integrate(n_iter=adapt_iters, points=adapt_points or points, seed=seed, rng="philox",
-                        precision=precision, adapt=2, reset_grid=True, assemble_result=False)
-    gpu_ms += r.stats["gpu_ms"]
-    pts += r.stats["unit_points"]
-    sw = np.zeros(len(recs))
-    swi = np.zeros(len(recs))
-    n = int(points)
-    res = None
-    for rnd in range(max_rounds):
-        r = integ.integrate(n_iter=replicates, points=n, seed=seed + 1 + rnd, rng="sobol", precision=precision,
-                            adapt=False, reset_grid=False, iter_offset=1000 + rnd * replicates,
-                            assemble_result=False)
-        gpu_ms += r.stats["gpu_ms"]
-        pts += r.stats["unit_points"]
-        for k, (unit, o) in enumerate(recs):
-            m, _ = integ.iterations(unit, replicates, o)
-            mu = float(np.mean(m))
-            var = float(np.var(m, ddof=1)) / replicates if replicates > 1 else 0.0
-            w = 1.0 / var if var > 0 else 1e300
-            sw[k] += w
-            swi[k] += w * mu
-        val = swi / sw
-        sig = np.sqrt(1.0 / sw)
-        R, E, values = _assembled(prep, recs, val, sig)
-        ratio = _worst_ratio(R, E, target, floor)
-        ok = ratio <= 1.0
-        res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=rnd + 1, points_per_replicate=n, values=R, errors=E,
-                   converged=ok, unit_values=val.copy(), unit_sigmas=sig.copy(), ratio=ratio)
-        if ok or 2 * n > max_points:
-            break
-        n *= 2
+                         max_rounds=12, seed=1, precision="fp64", floor=1e-2, max_points=1 << 24, max_gpu_s=None):
+    """Randomised quasi-Monte Carlo on adapted Vegas grids (FIESTA_METHOD_RQMC):
+    ``adapt_iters`` Philox iterations adapt the grids, then every round integrates each
+    unit with ``replicates`` independent digital shifts of a Sobol sequence of N points
+    (N = points, doubling per round up to ``max_points``); a result's round estimate is
+    the replicate mean, its error their spread over sqrt(replicates); rounds are
+    combined with inverse-variance weights.  Binary64 is the intended precision."""
+    res, _ = integrate_to_accuracy(integ, method="rqmc", target=target, floor=floor, points=points,
+                                   replicates=replicates, adapt_iters=adapt_iters, adapt_points=adapt_points or 0,
+                                   max_iters=max_rounds, seed=seed, precision=precision, max_points=max_points,
+                                   max_gpu_s=max_gpu_s or 0.0)
+    res["rounds"] = res["iterations"]
     return res
 
 
 def run_flow(integ, target=1e-4, points=1_000_000, keep=4096, train_rounds=8, steps_per_round=20, lr=2e-3,
              power=1, max_rounds=200, seed=1, precision="fp32", floor=1e-2, skip_rounds=None, max_gpu_s=None):
-    """Learned proposal: per unit, alternate flow sampling (an unbiased estimate each
-    round) and training on the round's kept points; stop when every eps order meets
-    the target (same rule as run_to_accuracy).  Rounds while training are combined
-    too, with inverse-variance weights, except the first ``skip_rounds`` (default:
-    half of the training rounds).  GPU seconds include the training."""
-    prep = integ.prep
-    recs = [(k, o) for k, u in enumerate(prep.units) for o in range(u.n_out)]
-    integ.flow_init(seed=seed)
+    """Learned proposal (FIESTA_METHOD_VEGAS with FIESTA_PROPOSAL_FLOW): per unit,
+    alternate flow sampling (an unbiased estimate each round) and training on the round's
+    kept points for the first ``train_rounds`` rounds; rounds from ``skip_rounds``
+    (default: half of the training rounds) on are combined with inverse-variance
+    weights; device time includes the training."""
     skip = train_rounds // 2 if skip_rounds is None else skip_rounds
-    sw = np.zeros(len(recs))
-    swi = np.zeros(len(recs))
-    gpu_ms = 0.0
-    pts = 0
-    res = None
-    for r in range(max_rounds):
-        m, v, st = integ.flow_sample(points, seed=seed, iteration=r, precision=precision,
-                                     keep=keep if r < train_rounds else 0)
-        gpu_ms += st["gpu_ms"]
-        pts += st["points"]
-        if r >= skip:
-            w = np.where(v > 0, 1.0 / np.maximum(v, 1e-300), 1e300)
-            sw += w
-            swi += w * m
-        if r < train_rounds:
-            _, tst = integ.flow_train(steps_per_round, lr=lr, power=power)
-            gpu_ms += tst["gpu_ms"]
-        if r < skip:
-            continue
-        val = swi / sw
-        sig = np.sqrt(1.0 / sw)
-        R, E, values = _assembled(prep, recs, val, sig)
-        ratio = _worst_ratio(R, E, target, floor)
-        ok = ratio <= 1.0
-        res = dict(gpu_s=gpu_ms * 1e-3, points=pts, rounds=r + 1, values=R, errors=E, converged=ok,
-                   unit_values=val.copy(), unit_sigmas=sig.copy(), ratio=ratio)
-        if (ok and r >= train_rounds) or (max_gpu_s and gpu_ms * 1e-3 >= max_gpu_s):
-            break
+    res, _ = integrate_to_accuracy(integ, method="vegas", proposal="flow", target=target, floor=floor, points=points,
+                                   keep=keep, train_rounds=train_rounds, steps_per_round=steps_per_round, lr=lr,
+                                   power=power, max_iters=max_rounds, seed=seed, precision=precision, skip=skip,
+                                   max_gpu_s=max_gpu_s or 0.0)
+    res["rounds"] = res["iterations"]
+    return res
+
+
+def allocate_points(prep, sig, n_used, values, target, floor, points):
+    """fiesta_allocate_points: Neyman allocation of ``points`` per unit for the assembled
+    series (per-result errors ``sig`` in the library's record order, points used so far
+    per unit ``n_used``, assembled values ``values`` by eps order setting the targets).
+    Marshalling only."""
+    lib = N.load()
+    opts, keep = accuracy_options(prep, target=target, floor=floor, points=points)
+    recs = _records(prep)
+    units = np.array([k for k, _ in recs], dtype=np.int64)
+    orders = np.array([_record_key(prep.units[k], o)[0] for k, o in recs], dtype=np.int32)
+    cost = np.array([len(u.program.code) + 4 * u.dim + 8 for u in prep.units], dtype=np.float64)
+    out = tuple(prep.out_orders)
+    re = np.array([complex(values.get(m, 0.0)).real for m in out])
+    im = np.array([complex(values.get(m, 0.0)).imag for m in out])
+    sig = np.ascontiguousarray(sig, dtype=np.float64)
+    n_used = np.ascontiguousarray(n_used, dtype=np.float64)
+    res = np.zeros(len(prep.units), dtype=np.int64)
+    dp = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+    N.check(lib.fiesta_allocate_points(C.byref(opts), len(prep.units), dp(cost), len(recs),
+                                       units.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       orders.ctypes.data_as(C.POINTER(C.c_int32)), dp(sig), dp(n_used), len(out),
+                                       dp(re), dp(im), res.ctypes.data_as(C.POINTER(C.c_int64))))
     return res

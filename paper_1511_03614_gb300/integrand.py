@@ -44,10 +44,11 @@ def _subsets(seq):
 class _SectorEval:
     """Shared pieces of one sector's integrands inside one Graph."""
 
-    def __init__(self, g: Graph, sec):
+    def __init__(self, g: Graph, sec, variables=None):
         self.g = g
         self.sec = sec
-        self.pos = {j: i for i, j in enumerate(sec.variables)}   # variable -> x index
+        # variable -> x index (a separate term is a function of fewer variables)
+        self.pos = {j: i for i, j in enumerate(variables if variables is not None else sec.variables)}
         self.S = singular(sec)
         self._pow = {}
         self._mono = {}
@@ -185,13 +186,16 @@ class _SectorEval:
             self._logt[j] = self.g.log(self.t(j))
         return self._logt[j]
 
-    def unit(self, K):
-        """Node of f_K; None when f_K is identically zero."""
+    def unit(self, K, only=None):
+        """Node of f_K (with ``only`` = T: of its T term alone); None when it is
+        identically zero."""
         g = self.g
         sec = self.sec
         S = self.S
         total = g.c(0.0)
         for T in _subsets(S):
+            if only is not None and tuple(sorted(T)) != tuple(sorted(only)):
+                continue
             top = K + len(T)
             if top < 0:
                 continue
@@ -245,6 +249,29 @@ def unit_graph(sec, K):
 
 def min_order(sec):
     return -len(singular(sec))
+
+
+def term_subsets(sec):
+    """The subsets T of the singular variables: the separately integrable terms of a
+    sector (the paper's SeparateTerms option, Sec. 4.4)."""
+    return list(_subsets(singular(sec)))
+
+
+def term_variables(sec, T):
+    """The variables a T term depends on (it is constant along T); at least one."""
+    return tuple(j for j in sec.variables if j not in T) or (sec.variables[0],)
+
+
+def term_graph(sec, orders, T):
+    """(Graph, result nodes) of the T term of every order in ``orders`` of one sector,
+    over the variables ``term_variables(sec, T)``; zero orders give constant 0."""
+    g = Graph()
+    ev = _SectorEval(g, sec, term_variables(sec, T))
+    outs = []
+    for K in orders:
+        node = ev.unit(K, only=T) if K >= -len(ev.S) else None
+        outs.append(g.c(0.0) if node is None else node)
+    return g, outs
 
 
 def sector_graph(sec, orders):

@@ -29,6 +29,7 @@ class Unit:
     cplx: bool = False        # deformed contour: results are (re, im) pairs, orders order .. order + n_out/2 - 1
     lam: float = None         # the deformation parameter of a complex unit
     sectors: tuple = None     # mixed units: the sectors whose integrands the program sums
+    term: tuple = None        # separate-term units: the variables whose pole term it is
 
 
 @dataclasses.dataclass
@@ -65,6 +66,34 @@ def _real_units(si, sec, Ks, fuse):
             continue
         g, out = r
         units.append(Unit(si, K, len(sec.variables), B.emit(g, out, len(sec.variables)), 0))
+    return units
+
+
+def _term_units(si, sec, Ks, fuse):
+    """Units of a sector with F > 0, one per separately integrable term (the paper's
+    SeparateTerms, Sec. 4.4): the term of a subset T of the singular variables is
+    constant along T, so it is integrated over the remaining variables only.  Fused:
+    one unit per term carrying the orders where it is non-zero; else one per (term,
+    order)."""
+    units = []
+    for T in I.term_subsets(sec):
+        var = I.term_variables(sec, T)
+        d = len(var)
+        if fuse:
+            g, outs = I.term_graph(sec, Ks, T)
+            nz = [k for k, o in enumerate(outs) if g.const_value(o) != 0.0]
+            if not nz:
+                continue
+            lo, hi = nz[0], nz[-1]
+            if hi - lo + 1 > MAX_OUT:
+                raise ValueError(f"a fused unit holds at most {MAX_OUT} orders")
+            units.append(Unit(si, Ks[lo], d, B.emit(g, outs[lo:hi + 1], d), 0, n_out=hi - lo + 1, term=tuple(T)))
+        else:
+            for K in Ks:
+                g, outs = I.term_graph(sec, [K], T)
+                if g.const_value(outs[0]) == 0.0:
+                    continue
+                units.append(Unit(si, K, d, B.emit(g, outs[0], d), 0, term=tuple(T)))
     return units
 
 
@@ -137,7 +166,8 @@ def _mix_units(secs, real, Ks_of, group, max_slots=72):
     return units
 
 
-def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=1.0, mix_sectors=1):
+def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=1.0, mix_sectors=1,
+                    separate_terms=False):
     """Units of a Feynman integral; with ``fuse_orders`` one unit per sector carries all
     its eps orders (a vector-valued integrand with one Vegas grid).
 
@@ -148,7 +178,11 @@ def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=
     A sector where no parameter keeps Im F <= 0 raises ValueError.
     ``mix_sectors`` > 1 sums that many consecutive real sectors of equal dimension into
     one program with all their orders (the paper's MixSectors; implies fused orders).
+    ``separate_terms`` gives every real sector one unit per separately integrable term
+    (the paper's SeparateTerms, ``_term_units``); it excludes ``mix_sectors``.
     """
+    if separate_terms and mix_sectors > 1:
+        raise ValueError("separate_terms and mix_sectors exclude each other")
     U, F = symanzik(problem)
     n = len(problem.propagators)
     L = len(problem.loop_momenta)
@@ -165,7 +199,9 @@ def prepare_feynman(problem, strategy="M", fuse_orders=False, lam=None, lam_max=
         if not Ks:
             continue
         if lm is None:
-            if mix_sectors <= 1:
+            if separate_terms:
+                units += _term_units(si, sec, Ks, fuse_orders)
+            elif mix_sectors <= 1:
                 units += _real_units(si, sec, Ks, fuse_orders)
         else:
             units += _complex_units(si, sec, Ks, fuse_orders, lm)

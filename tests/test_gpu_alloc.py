@@ -78,3 +78,66 @@ def test_rqmc_replicates_reach_the_closed_form():
     exact = {-2: 2.0, -1: -math.log(2.0), 0: -2 * math.pi ** 2 / 3}
     for n, v in exact.items():
         assert abs(r["values"][n] - v) < 4 * r["errors"][n] + 1e-12, (n, r["values"][n], v, r["errors"][n])
+
+
+def test_vegas_loop_combines_every_counted_iteration():
+    """fiesta_integrate_to_accuracy one call at a time (max_calls = 1): after each call the
+    running sums hold exactly the inverse-variance sums of every iteration but the first
+    (skip = 1), the per-iteration results being those fiesta_iterations reports for the
+    call; the returned unit values and sigmas are swi / sw and sqrt(1 / sw)."""
+    need_gpu()
+    from paper_1511_03614_gb300 import prepare_feynman, Integrator
+    from paper_1511_03614_gb300.api import integrate_to_accuracy, _records
+    import workloads as W
+    integ = Integrator(prepare_feynman(W.bubble()))
+    recs = _records(integ.prep)
+    sw, swi = np.zeros(len(recs)), np.zeros(len(recs))
+    state = None
+    for call in range(3):
+        res, state = integrate_to_accuracy(integ, state, method="vegas", target=1e-12, points=20_000,
+                                           iters_per_call=2, max_iters=6, skip=1, max_calls=1, seed=3)
+        for k, (u, o) in enumerate(recs):
+            m, v = integ.iterations(u, 2, o)
+            for j in range(2):
+                if 2 * call + j >= 1:
+                    sw[k] += 1.0 / v[j]
+                    swi[k] += m[j] / v[j]
+        assert state[0].iterations == 2 * (call + 1)
+        assert np.allclose(state[1]["sw"], sw, rtol=1e-13, atol=0) and np.allclose(state[1]["swi"], swi, rtol=1e-12)
+    assert np.allclose(res["unit_values"], swi / sw, rtol=1e-12)
+    assert np.allclose(res["unit_sigmas"], np.sqrt(1.0 / sw), rtol=1e-12)
+
+
+def test_rqmc_loop_uses_the_replicate_spread():
+    """One round of FIESTA_METHOD_RQMC: each result's estimate is the mean of its
+    replicates and its variance their sample variance over the replicate count."""
+    need_gpu()
+    from paper_1511_03614_gb300 import prepare_feynman, Integrator
+    from paper_1511_03614_gb300.api import integrate_to_accuracy, _records
+    import workloads as W
+    integ = Integrator(prepare_feynman(W.box(), fuse_orders=True))
+    recs = _records(integ.prep)
+    res, state = integrate_to_accuracy(integ, method="rqmc", target=1e-12, points=1 << 12, replicates=8,
+                                       adapt_iters=2, max_iters=1, seed=5)
+    for k, (u, o) in enumerate(recs):
+        m, _ = integ.iterations(u, 8, o)
+        var = np.var(m, ddof=1) / 8
+        assert math.isclose(res["unit_values"][k], np.mean(m), rel_tol=1e-12, abs_tol=1e-15)
+        assert math.isclose(res["unit_sigmas"][k], math.sqrt(var), rel_tol=1e-9)
+    assert state[0].points_per_replicate == 1 << 12
+
+
+def test_flow_proposal_in_fiesta_integrate():
+    """fiesta_options.proposal = FLOW: iterations drawn from the units' flows, trained
+    between iterations; the box's closed form within 4 sigma of the combined result."""
+    need_gpu()
+    from paper_1511_03614_gb300 import prepare_feynman, Integrator
+    import workloads as W
+    integ = Integrator(prepare_feynman(W.box(), fuse_orders=True))
+    res = integ.integrate(n_iter=6, points=400_000, seed=4, precision="fp32", proposal="flow",
+                          flow_train_steps=10, skip_first=True)
+    exact = {-2: 2.0, -1: -math.log(2.0), 0: -2 * math.pi ** 2 / 3}
+    for n, v in exact.items():
+        s = res.assembled_errors[n]
+        assert 0 < s < 5e-3 and abs(res.assembled[n] - v) < 4 * s, (n, res.assembled[n], v, s)
+    assert res.stats["kernels_launched"] > 6

@@ -180,27 +180,6 @@ def test_combine_shards_complex_records():
     assert v[0] == 3.0 and abs(e[0] - 1.0) < 1e-15
 
 
-def test_allocate_points_neyman():
-    """Neyman allocation: with equal spreads the points go as 1/sqrt(cost); a unit
-    with four times the variance gets twice the points; the total cost is that of the
-    uniform allocation (before clamping)."""
-    import numpy as np
-    from paper_1511_03614_gb300.api import allocate_points
-    prep = prepare_feynman(W.box())
-    nu = len(prep.units)
-    values = {-2: 2.0, -1: -0.69, 0: -6.58}
-    sig = np.full(nu, 1e-3)
-    n_used = np.full(nu, 1e6)
-    N = allocate_points(prep, sig, n_used, values, 1e-4, 1e-2, 100_000, lo_frac=0.0, hi_mult=1e9)
-    cost = np.array([len(u.program.code) + 4 * u.dim + 8 for u in prep.units], dtype=float)
-    assert abs(np.sum(N * cost) / (100_000 * cost.sum()) - 1) < 1e-3
-    sig2 = sig.copy()
-    sig2[3] *= 2.0
-    N2 = allocate_points(prep, sig2, n_used, values, 1e-4, 1e-2, 100_000, lo_frac=0.0, hi_mult=1e9)
-    ratio = (N2[3] / N2[4]) / (N[3] / N[4])
-    assert abs(ratio - 2.0) < 0.01, ratio
-
-
 def test_no_cpu_fallback():
     """Without a GPU the product path refuses to run (no silent CPU fallback)."""
     import torch
@@ -255,3 +234,34 @@ def test_corner_differences_vanish_exactly_at_the_boundary():
         X = rng.choice(vals, size=(400, u.dim)).astype(np.float32).astype(np.float64)
         f = run(u.program, X, np.float32)
         assert np.all(np.isfinite(f)), k
+
+
+@pytest.mark.parametrize("name,fuse", [("box", False), ("box", True), ("double_box", True)])
+def test_separate_term_programs_match_oracle(name, fuse):
+    """SeparateTerms units: each program (over the variables outside its term's set T)
+    computes the oracle's T term of its sector at every order it carries."""
+    prob = getattr(W, name)()
+    prep = prepare_feynman(prob, fuse_orders=fuse, separate_terms=True)
+    rng = np.random.default_rng(8)
+    idx = range(len(prep.units)) if name == "box" else rng.choice(len(prep.units), 12, replace=False)
+    orc_units = {}
+    from oracle import sectors as OS
+    full = P.feynman_problem(prob) if name == "box" else None
+    secs = full.sectors if full is not None else None
+    if secs is None:
+        from oracle.uf import symanzik as osym
+        U, F, xs = osym(prob)
+        prim = OS.primary_sectors(U, F, xs, prob.indices, len(prob.loop_momenta))
+        secs = [s for p in prim for s in OS.decompose(p, "M")]
+    for i in idx:
+        u = prep.units[i]
+        sec = secs[u.sector]
+        X = rng.uniform(0.05, 1.0, size=(16, u.dim))
+        Fv = run(u.program, X)
+        Fv = Fv[:, None] if Fv.ndim == 1 else Fv
+        for k in range(u.n_out):
+            e = OS.unit_integrand(sec, u.order + k, term=u.term)
+            var = tuple(j for j in sec.variables if j not in u.term) or (sec.variables[0],)
+            o = P.Unit(u.sector, u.order + k, var, e)
+            assert o.dim == u.dim
+            assert np.all(np.abs(Fv[:, k] - o.f_numpy(X)) <= 1e-13 * P.magnitude_numpy(o, X)), (i, k)
