@@ -60,7 +60,10 @@ def parse():
     ap.add_argument("--fuse", type=int, default=1, help="1: one unit per sector carrying all its eps orders")
     ap.add_argument("--forms", default="fp64,auto,fp32,fp64_alloc,auto_alloc,rqmc_fp64,flow_fp32,cuhre_fp64",
                     help="tta mode: comma-separated forms to run")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre"],
+    ap.add_argument("--threads", type=int, default=256, help="kernel mode: threads per block")
+    ap.add_argument("--ppt", type=int, default=8, help="kernel mode: points per thread per work item")
+    ap.add_argument("--units", type=int, default=0, help="kernel mode, stress: the first N integrands (0: all)")
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre", "kernel"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
     ap.add_argument("--target", type=float, default=1e-4)
     ap.add_argument("--max-iters", type=int, default=400, help="tta mode: Vegas iteration cap per form")
@@ -709,10 +712,38 @@ def run_cuhre(args):
                                   for n in res.assembled}}))
 
 
+def run_kernel(args):
+    """Two evaluation passes at a fixed launch shape (no autotuner, no graph): the second
+    is the launch a profiler captures with -k regex:k_eval -s 1 -c 1.  Prints the pass's
+    device time and rate.  Not a bench line."""
+    import torch
+    import workloads as W
+    from paper_1511_03614_gb300 import Integrator, prepare_direct
+    torch.cuda.set_device(0)
+    if args.workload == "stress":
+        prep = prepare_direct(W.stress_suite(args.units or 10_000), "stress")
+        rng = "sobol"
+    else:
+        prep = prepared(args.workload, args.fuse)
+        rng = "philox"
+    pts = args.points or 200_000
+    ig = Integrator(prep)
+    for s in range(2):
+        r = ig.integrate(n_iter=1, points=pts, seed=1 + s, rng=rng, adapt=2, threads=args.threads,
+                         points_per_thread=args.ppt, precision=args.precision, graph=False,
+                         accumulate="registers" if args.workload != "stress" else "auto")
+    print(json.dumps({"mode": "kernel", "workload": args.workload, "precision": args.precision, "points": pts,
+                      "units": len(prep.units), "threads": args.threads, "ppt": args.ppt,
+                      "eval_ms": r.stats["eval_ms"],
+                      "unit_points_per_s": r.stats["unit_points"] / (r.stats["eval_ms"] * 1e-3)}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "kernel":
+        run_kernel(args)
     elif args.mode == "tta":
         run_tta(args)
     elif args.mode == "cuhre":
