@@ -362,3 +362,25 @@ def test_graph_replay_matches_direct_launches():
     for x, y, z in zip(a.per_unit, b.per_unit, c.per_unit):
         assert x["value"] == y["value"] == z["value"] and x["sigma"] == y["sigma"] == z["sigma"]
     assert b.stats["eval_ms"] > 0 and c.stats["eval_ms"] > 0
+
+
+def test_whole_unit_items_same_points():
+    """With many more units than resident blocks (1300 stress integrands on 152 SMs) a work
+    item is a whole unit: the same Sobol points and sums as the oracle, and the same
+    means as the chunked schedule of a small slice of the same units."""
+    need_gpu()
+    probs, prep, integ = stress(1300)
+    N = 4096
+    integ.integrate(n_iter=1, points=N, seed=17, rng="sobol", adapt=False)
+    whole = {k: integ.iterations(k, 1)[0][0] for k in range(0, 1300, 97)}
+    for k in list(whole)[:8]:
+        o = P.direct_problem(probs[k]).units[0]
+        r = V.integrate_unit(o.f_numpy, o.dim, 1, N, 17, prep.units[k].rng_key, rng="sobol", adapt=False)
+        U = V.sobol.uniforms(17, prep.units[k].rng_key, 0, 0, N, o.dim)
+        X, J, _ = V.vegas_map(r.grids[0], U)
+        absum = np.mean(np.abs(o.f_numpy(X) * J))
+        assert abs(whole[k] - r.iters[0][0]) <= 1e-11 * absum, k
+    integ.integrate(n_iter=1, points=N, seed=17, rng="sobol", adapt=False, units=(0, 98), assemble_result=False)
+    for k in (0, 97):
+        m = integ.iterations(k, 1)[0][0]
+        assert abs(m - whole[k]) <= 1e-13 * abs(m) + 1e-300, k
