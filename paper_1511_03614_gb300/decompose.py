@@ -174,8 +174,5 @@ def singular(sec):
         if c <= -1:
             if b == 0:
                 raise ValueError(f"unregulated endpoint singularity in t{j}")
-            if c < -1:
-                raise NotImplementedError("poles of order > 1 in one variable (t^{-2-...}) are not supported "
-                                          "by the bytecode emitter")
             out.append(j)
     return tuple(out)

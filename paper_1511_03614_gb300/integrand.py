@@ -189,6 +189,8 @@ class _SectorEval:
     def unit(self, K, only=None):
         """Node of f_K (with ``only`` = T: of its T term alone); None when it is
         identically zero."""
+        if any(self.sec.mono[j][0] < -1 for j in self.S):
+            return self._unit_general(K, only)
         g = self.g
         sec = self.sec
         S = self.S
@@ -225,6 +227,212 @@ class _SectorEval:
                 if j not in T:
                     term = g.mul(term, g.inv(self.t(j)))
             total = g.add(total, term)
+        if g.const_value(total) == 0.0:
+            return None
+        mono = g.c(float(sec.coef))
+        for j in sec.variables:
+            if j in S:
+                continue
+            c = sec.mono[j][0]
+            if c:
+                mono = g.mul(mono, g.powi(self.t(j), c))
+        return g.mul(total, mono)
+
+
+    # -- poles of higher order: Taylor subtraction of order p_j in t_j --------------------
+    #
+    # For t^{-1-p+b eps} G the subtraction at t = 0 keeps the Taylor polynomial of G of
+    # degree p:  int_0^1 t^{-1-p+b eps} G = int_0^1 t^{-1-p+b eps} (G - sum_{k<=p} t^k G_k)
+    # + sum_{k<=p} G_k / (k - p + b eps),  G_k the k-th Taylor coefficient at t = 0.  Over
+    # several singular variables the pole terms T (with their coefficient orders k_T) and
+    # the remainders of the others multiply out; the Taylor coefficients of G_N are taken
+    # from truncated multivariate power series of the polynomials (products, the series
+    # inverse and the series logarithm).  p = 0 everywhere is the corner form above.
+
+    def _poly_series(self, i, spec):
+        """Series of P_i in the variables of ``spec`` with order >= 1 (truncated at those
+        orders), the variables of order 0 set to 0: {multi-index: node}."""
+        V = [j for j in sorted(spec) if spec[j] >= 1]
+        zero = {j for j in spec if spec[j] == 0}
+        p = self.sec.polys[i][0]
+        groups = {}
+        for m, c in p.items():
+            if any(m[j - 1] for j in zero):
+                continue
+            idx = tuple(m[j - 1] for j in V)
+            if any(e > spec[j] for e, j in zip(idx, V)):
+                continue
+            rest = tuple(0 if (q + 1) in V else e for q, e in enumerate(m))
+            groups.setdefault(idx, []).append((rest, c))
+        out = {}
+        for idx, terms in sorted(groups.items()):
+            acc = self.g.c(0.0)
+            for rest, c in sorted(terms):
+                acc = self.g.fma(self.monomial(rest), self.g.c(float(c)), acc)
+            out[idx] = acc
+        return V, out
+
+    @staticmethod
+    def _indices(V, spec):
+        return sorted(itertools.product(*[range(spec[j] + 1) for j in V]), key=lambda m: (sum(m), m))
+
+    def _smul(self, A, B, V, spec):
+        g = self.g
+        out = {}
+        for m in self._indices(V, spec):
+            acc = g.c(0.0)
+            for l, a in A.items():
+                r = tuple(x - y for x, y in zip(m, l))
+                if min(r, default=0) < 0 or r not in B:
+                    continue
+                acc = g.fma(a, B[r], acc)
+            if g.const_value(acc) != 0.0:
+                out[m] = acc
+        return out
+
+    def _sinv(self, A, V, spec):
+        g = self.g
+        z = tuple(0 for _ in V)
+        b0 = g.inv(A[z])
+        out = {z: b0}
+        for m in self._indices(V, spec):
+            if m == z:
+                continue
+            acc = g.c(0.0)
+            for l, a in A.items():
+                if l == z:
+                    continue
+                r = tuple(x - y for x, y in zip(m, l))
+                if min(r, default=0) < 0 or r not in out:
+                    continue
+                acc = g.fma(a, out[r], acc)
+            if g.const_value(acc) != 0.0:
+                out[m] = g.neg(g.mul(acc, b0))
+        return out
+
+    def _spow(self, A, a, V, spec):
+        z = tuple(0 for _ in V)
+        if a < 0:
+            A, a = self._sinv(A, V, spec), -a
+        out = {z: self.g.c(1.0)}
+        for _ in range(int(a)):
+            out = self._smul(out, A, V, spec)
+        return out
+
+    def _slog(self, A, V, spec):
+        g = self.g
+        z = tuple(0 for _ in V)
+        inv0 = g.inv(A[z])
+        u = {m: g.mul(a, inv0) for m, a in A.items() if m != z}
+        out = {z: g.log(A[z])}
+        power = dict(u)
+        for n in range(1, sum(spec[j] for j in V) + 1):
+            for m, v in power.items():
+                out[m] = g.fma(v, g.c((-1.0) ** (n + 1) / n), out.get(m, g.c(0.0)))
+            power = self._smul(power, u, V, spec)
+        return out
+
+    def G_coeff(self, N, spec):
+        """The Taylor coefficient of G_N of order spec[j] in each variable j of ``spec``
+        (order 0: G_N at t_j = 0)."""
+        key = ("GC", N, tuple(sorted(spec.items())))
+        if key in self._corner:
+            return self._corner[key]
+        if all(k == 0 for k in spec.values()):
+            out = self.G_at(N, tuple(sorted(spec)))
+            self._corner[key] = out
+            return out
+        g = self.g
+        V = [j for j in sorted(spec) if spec[j] >= 1]
+        z = tuple(0 for _ in V)
+        G = {z: g.c(1.0)}
+        L = {}
+        for i, (p, (a0, a1)) in enumerate(self.sec.polys):
+            _, Pi = self._poly_series(i, spec)
+            if a0:
+                G = self._smul(G, self._spow(Pi, a0, V, spec), V, spec)
+            if a1:
+                Li = self._slog(Pi, V, spec)
+                for m, v in Li.items():
+                    L[m] = g.fma(v, g.c(float(a1)), L.get(m, g.c(0.0)))
+        for i, power in self.sec.log_factor:
+            _, Pi = self._poly_series(i, spec)
+            G = self._smul(G, self._spow(self._slog(Pi, V, spec), power, V, spec), V, spec)
+        for n in range(1, N + 1):
+            G = {m: g.mul(v, g.c(1.0 / n)) for m, v in self._smul(G, L, V, spec).items()}
+        out = G.get(tuple(spec[j] for j in V), g.c(0.0))
+        self._corner[key] = out
+        return out
+
+    def _unit_general(self, K, only):
+        g = self.g
+        sec = self.sec
+        S = self.S
+        p = {j: -1 - sec.mono[j][0] for j in S}
+        nmax = K + len(S)
+
+        def smul(a, b):
+            out = {}
+            for i, x in a.items():
+                for j, y in b.items():
+                    if i + j <= nmax:
+                        out[i + j] = g.fma(x, y, out.get(i + j, g.c(0.0)))
+            return out
+
+        total = g.c(0.0)
+        for T in _subsets(S):
+            if only is not None and tuple(sorted(T)) != tuple(sorted(only)):
+                continue
+            rest = [j for j in S if j not in T]
+            for ks in itertools.product(*[range(p[j] + 1) for j in T]):
+                coef = {0: g.c(1.0)}
+                for j, k in zip(T, ks):
+                    b = sec.mono[j][1]
+                    if k == p[j]:
+                        s = {-1: g.c(1.0 / (math.factorial(k) * b))}
+                    else:
+                        q = k - p[j]
+                        s = {m: g.c((1.0 / (math.factorial(k) * q)) * (-b / q) ** m) for m in range(0, nmax + 2)}
+                    coef = smul(coef, s)
+                for j in sec.variables:
+                    b = sec.mono[j][1]
+                    if j in T or not b:
+                        continue
+                    lt = g.mul(self.logt(j), g.c(float(b)))
+                    s, pw = {0: g.c(1.0)}, g.c(1.0)
+                    for m in range(1, nmax + 2):
+                        pw = g.mul(pw, g.mul(lt, g.c(1.0 / m)))
+                        s[m] = pw
+                    coef = smul(coef, s)
+                term = g.c(0.0)
+                for m, cm in sorted(coef.items()):
+                    n = K - m
+                    if not 0 <= n <= nmax or g.const_value(cm) == 0.0:
+                        continue
+                    # remainders of the rest: sum over Z subset rest and orders k_Z of
+                    # (-1)^|Z| prod_{j in Z} t_j^k_j  x  the Taylor coefficient
+                    op = g.c(0.0)
+                    for Z in _subsets(rest):
+                        for kz in itertools.product(*[range(p[j] + 1) for j in Z]):
+                            spec = {j: k for j, k in zip(T, ks)}
+                            spec.update({j: k for j, k in zip(Z, kz)})
+                            c = self.G_coeff(n, spec)
+                            if g.const_value(c) == 0.0:
+                                continue
+                            fac = g.c((-1.0) ** len(Z))
+                            for j, k in zip(Z, kz):
+                                if k:
+                                    fac = g.mul(fac, self.tpow(j, k))
+                            op = g.fma(fac, c, op)
+                    term = g.fma(cm, op, term)
+                if g.const_value(term) == 0.0:
+                    continue
+                for j, k in zip(T, ks):                   # d^k/dt^k at 0 = k! x coefficient
+                    if k:
+                        term = g.mul(term, g.c(float(math.factorial(k))))
+                for j in rest:
+                    term = g.mul(term, g.powi(self.t(j), sec.mono[j][0]))
+                total = g.add(total, term)
         if g.const_value(total) == 0.0:
             return None
         mono = g.c(float(sec.coef))

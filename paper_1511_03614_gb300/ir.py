@@ -90,6 +90,8 @@ class Graph:
         ca, cb = self.const_value(a), self.const_value(b)
         if ca == 0.0 or cb == 0.0:
             return acc
+        if ca is not None and cb is not None:
+            return self.add(self.c(ca * cb), acc)
         if ca == 1.0:
             return self.add(b, acc)
         if cb == 1.0:

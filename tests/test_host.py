@@ -265,3 +265,24 @@ def test_separate_term_programs_match_oracle(name, fuse):
             o = P.Unit(u.sector, u.order + k, var, e)
             assert o.dim == u.dim
             assert np.all(np.abs(Fv[:, k] - o.f_numpy(X)) <= 1e-13 * P.magnitude_numpy(o, X)), (i, k)
+
+
+def test_higher_pole_programs_match_oracle():
+    """Sectors with a pole of order 2 (Taylor subtraction of order 1, composed with an
+    order-0 one in the 2-dimensional cases): every program against the oracle's
+    integrand at 50 digits, within 64 u M."""
+    import mpmath as mp
+    for prob in W.higher_pole_suite():
+        prep = prepare_direct([prob])
+        orc = P.direct_problem(prob)
+        by = {(u.sector, u.order): u for u in orc.units}
+        assert len(prep.units) == len(orc.units)
+        rng = np.random.default_rng(13)
+        for u in prep.units:
+            o = by[(u.sector, u.order)]
+            X = np.concatenate([rng.uniform(0.05, 1.0, size=(12, u.dim)), np.exp2(-rng.uniform(1, 20, (8, u.dim)))])
+            f = run(u.program, X)
+            with mp.workdps(50):
+                ref = np.array([float(o.f_mp(x, 50)) for x in X])
+            M = P.magnitude_numpy(o, X)
+            assert np.all(np.abs(f - ref) <= 64 * 2.0 ** -53 * M), (prob.name, u.order)

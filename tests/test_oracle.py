@@ -461,3 +461,29 @@ def test_separate_terms_integrate_to_the_closed_form(name):
         exact = {-2: 2.0, -1: -math.log(2.0), 0: -2 * math.pi ** 2 / 3}
     for n, v in exact.items():
         assert abs(R[n] - v) < 1e-9, (n, R[n], v)
+
+
+def test_higher_pole_subtraction_in_two_variables():
+    """x1^{-2+eps}(1+x1)^-1 x2^{-1+eps}(1+x2)^-1 over the square: the p = 1 and p = 0
+    subtractions composed (every pole term T with its Taylor orders, the remainders of
+    the rest) integrate to the product beta(-1+eps) beta(eps), beta(s) =
+    int_0^1 t^{s-1}/(1+t) dt = (psi((s+1)/2) - psi(s/2))/2."""
+    prob = W.higher_pole_suite()[1]
+    pr = P.direct_problem(prob)
+    beta = lambda s: (mp.digamma((s + 1) / 2) - mp.digamma(s / 2)) / 2
+    with mp.workdps(30):
+        c = mp.taylor(lambda e: e * e * beta(-1 + e) * beta(e), 0, 4, method="quad", radius=0.2)
+    # the subtracted integrands cancel like t near 0: integrate values taken at 60 digits
+    for K in prob.orders:
+        tot = mp.mpf(0)
+        for u in pr.units:
+            if u.order != K:
+                continue
+            fn0 = sp.lambdify([S.tsym(j) for j in u.variables], u.expr, "mpmath")
+
+            def fn(*x, fn0=fn0):
+                with mp.workdps(60):
+                    return fn0(*x)
+            with mp.workdps(20):
+                tot += mp.quad(fn, *[[0, 1]] * u.dim)
+        assert abs(tot - c[K + 2]) < 1e-12 * max(1, abs(c[K + 2])), (K, tot, c[K + 2])

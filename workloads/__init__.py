@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "FeynmanProblem", "DirectProblem", "DirectFactor",
     "bubble", "box", "box_physical", "box_paper_example", "double_box", "double_box_alt_routing",
-    "stress_suite", "STRESS_SEED",
+    "stress_suite", "STRESS_SEED", "higher_pole_suite",
 ]
 
 
@@ -154,6 +154,23 @@ class DirectProblem:
     factors: tuple
     log_power: int
     orders: tuple
+
+
+def higher_pole_suite():
+    """Direct integrands with a pole of order 2 in one variable (t^{-2+eps}), the case
+    the Taylor subtraction of order p >= 1 covers: x^{-2+eps}/(1+x); the separable
+    x1^{-2+eps}(1+x1)^-1 x2^{-1+eps}(1+x2)^-1; and a non-separable 2-dimensional one."""
+    F = DirectFactor
+    one_plus = lambda dim, j: F(((1.0, (0,) * dim), (1.0, tuple(int(i == j) for i in range(dim)))), -1, 0)
+    eps_pow = lambda dim, j, m: F(((1.0, tuple(int(i == j) for i in range(dim))),), 0, m)
+    return (
+        DirectProblem("pole2_1d", 1, (-2,), (eps_pow(1, 0, 1), one_plus(1, 0)), 0, (-1, 0, 1, 2)),
+        DirectProblem("pole2_separable", 2, (-2, -1), (eps_pow(2, 0, 1), eps_pow(2, 1, 1), one_plus(2, 0),
+                                                      one_plus(2, 1)), 0, (-2, -1, 0, 1)),
+        DirectProblem("pole2_mixed", 2, (-2, -1), (eps_pow(2, 0, 1), eps_pow(2, 1, 2),
+                                                   F(((1.0, (0, 0)), (0.5, (1, 0)), (0.25, (0, 1)), (0.3, (1, 1))),
+                                                     -2, 1)), 0, (-2, -1, 0, 1)),
+    )
 
 
 STRESS_SEED = 1511036140
