@@ -218,9 +218,11 @@ def op_costs32(peaks):
 # (workload, precision, fused); the kernel stages programs, constants and grids in shared
 # memory, so this does not grow with the number of points.  None: not captured for
 # the current kernel.
-TRAFFIC = {("box", "fp64", True): (110336, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                             "k_eval<double, Philox, 6> launch on the fused box (12 units x 2e5 "
-                                             "points)")}
+TRAFFIC = {("double_box", "fp64", True): (
+    3988992, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_eval<double, Philox, 6, registers> launch "
+             "on the fused double box at 2e5 points per unit (bench.py --mode kernel --workload double_box --points "
+             "200000 --threads 256 --ppt 8); programs, constants and grids stay L2-resident across block visits, so "
+             "the DRAM bytes do not grow with the points per unit")}
 
 
 def roofline_of(prep, res, peaks, pts, pass_s, args, iters):
