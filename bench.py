@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=256, help="kernel mode: threads per block")
     ap.add_argument("--ppt", type=int, default=8, help="kernel mode: points per thread per work item")
     ap.add_argument("--units", type=int, default=0, help="kernel mode, stress: the first N integrands (0: all)")
+    ap.add_argument("--max-slots", type=int, default=0,
+                    help="kernel mode: only the units whose programs need at most this many slots (0: all)")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre", "kernel"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
     ap.add_argument("--target", type=float, default=1e-4)
@@ -393,7 +395,9 @@ def run_ours(args):
                        "results_per_point": sum(u.n_out for u in prep.units) / len(prep.units),
                        "units_fp32": res.stats.get("units_fp32") if res else None,
                        "launch_shape": {"threads": res.stats.get("threads"),
-                                        "points_per_thread": res.stats.get("points_per_thread")} if res else None,
+                                        "points_per_thread": res.stats.get("points_per_thread"),
+                                        "wide_threads": res.stats.get("wide_threads"),
+                                        "eval_groups": res.stats.get("eval_groups")} if res else None,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)"},
             "roofline": roofline,
@@ -728,6 +732,9 @@ def run_kernel(args):
     else:
         prep = prepared(args.workload, args.fuse)
         rng = "philox"
+    if args.max_slots:
+        import dataclasses
+        prep = dataclasses.replace(prep, units=[u for u in prep.units if u.program.n_slots <= args.max_slots])
     pts = args.points or 200_000
     ig = Integrator(prep)
     for s in range(2):

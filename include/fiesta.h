@@ -104,7 +104,9 @@ typedef struct {
     int64_t unit_begin;       /* integrate units [unit_begin, unit_end) only ... */
     int64_t unit_end;         /* ... unit_end <= 0 means all units */
     int64_t timeout_ms;       /* device time budget per kernel launch; 0 = none */
-    int32_t threads;          /* threads per block (multiple of 32, <= 256; a power of two with Sobol); 0 = autotuned */
+    int32_t threads;          /* threads per block (multiple of 32, <= 256, or <= 512 for fused units with
+                                 register sums; a power of two with Sobol); 0 = autotuned, which also splits
+                                 a precision's fused units by slot count (see fiesta_stats.wide_threads) */
     int32_t reset_grid;       /* nonzero: start from the uniform grid (else keep the last one) */
     int32_t iter_offset;      /* added to the iteration number in the point streams */
     int32_t points_per_thread;/* points per thread per work item; 0 = autotuned */
@@ -172,10 +174,16 @@ typedef struct {
     int64_t units_fp32;       /* units evaluated in binary32 */
     int64_t unit_points;      /* evaluations of (sector, order) integrands: points x results, a
                                  complex unit's (re, im) pair counting as one */
-    int32_t threads[2];       /* block size used for binary64 [0] and binary32 [1] */
+    int32_t threads[2];       /* block size used for binary64 [0] and binary32 [1] (when a precision's
+                                 units were split by slot count: that of the units with the most slots) */
     int32_t points_per_thread[2];
     int64_t points_ext;       /* points promoted near the boundary (small_x: binary64 -> double-double,
                                  small_x32: binary32 -> binary64) */
+    int32_t wide_threads[2];  /* block size of the fused units with few slots when a precision's units
+                                 were split by slot count (their slot files fit 512-thread blocks and the
+                                 others' do not); 0: not split */
+    int32_t eval_groups;      /* evaluation launches per iteration (one per precision and slot group) */
+    int32_t pad;
 } fiesta_stats;
 
 typedef struct fiesta_ctx fiesta_ctx;
@@ -531,6 +539,15 @@ int fiesta_flow_check(fiesta_ctx *ctx, int64_t unit, int64_t n, int32_t precisio
 void fiesta_free(fiesta_ctx *ctx);
 const char *fiesta_last_error(void);
 int fiesta_version(void);
+
+/* Sizes in bytes of this header's structures as the library was compiled, for a binding
+ * to check its own layouts against (no counterpart in the method; host only, no device
+ * call).  sizes (host, caller-owned, n entries) receives, as far as n reaches:
+ * fiesta_program, fiesta_alloc, fiesta_options, fiesta_unit_result, fiesta_stats,
+ * fiesta_accuracy_options, fiesta_accuracy_state, fiesta_cuhre_options,
+ * fiesta_cuhre_result.  Returns the number of structures (9); -1 for a null array
+ * with n > 0. */
+int fiesta_abi_sizes(int64_t *sizes, int32_t n);
 
 #ifdef __cplusplus
 }

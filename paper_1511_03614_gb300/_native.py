@@ -76,7 +76,8 @@ class Stats(C.Structure):
     _fields_ = [("gpu_ms", C.c_double), ("eval_ms", C.c_double), ("points", C.c_int64),
                 ("points_per_s", C.c_double), ("kernels_launched", C.c_int32), ("eval_launches", C.c_int32),
                 ("units_fp32", C.c_int64), ("unit_points", C.c_int64), ("threads", C.c_int32 * 2),
-                ("points_per_thread", C.c_int32 * 2), ("points_ext", C.c_int64)]
+                ("points_per_thread", C.c_int32 * 2), ("points_ext", C.c_int64),
+                ("wide_threads", C.c_int32 * 2), ("eval_groups", C.c_int32), ("pad", C.c_int32)]
 
 
 class CuhreOptions(C.Structure):
@@ -139,7 +140,12 @@ EXPORTS = {
     "fiesta_free": (None, [C.c_void_p]),
     "fiesta_last_error": (C.c_char_p, []),
     "fiesta_version": (C.c_int, []),
+    "fiesta_abi_sizes": (C.c_int, [C.POINTER(C.c_int64), C.c_int32]),
 }
+
+# the ctypes mirrors in the order fiesta_abi_sizes reports the C structures
+ABI_STRUCTS = ("Program", "Alloc", "Options", "UnitResult", "Stats", "AccuracyOptions", "AccuracyState",
+               "CuhreOptions", "CuhreResult")
 
 _lib = None
 

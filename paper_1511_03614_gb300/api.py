@@ -165,7 +165,8 @@ class Integrator:
         stats = dict(gpu_ms=st.gpu_ms, eval_ms=st.eval_ms, points=st.points, points_per_s=st.points_per_s,
                      kernels_launched=st.kernels_launched, eval_launches=st.eval_launches,
                      units_fp32=st.units_fp32, unit_points=st.unit_points, threads=tuple(st.threads),
-                     points_per_thread=tuple(st.points_per_thread), points_ext=st.points_ext)
+                     points_per_thread=tuple(st.points_per_thread), points_ext=st.points_ext,
+                     wide_threads=tuple(st.wide_threads), eval_groups=st.eval_groups)
         res = Result(values, errors, pu, stats)
         if assemble_result and units is None:
             res.assembled, res.assembled_errors = assemble_records(self.prep, *recs)

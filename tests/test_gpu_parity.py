@@ -97,6 +97,33 @@ def test_fused_double_box_same_point_sums(accumulate, threads):
             assert abs(m[0] - np.mean(v)) <= bound, (int(i), k, m[0], np.mean(v), bound)
 
 
+def test_slot_groups_same_point_sums():
+    """With the launch shape left to the autotuner, the fused double box's binary64 units
+    run in two launches per iteration, split by slot count (the units whose slot files
+    fit 512-thread blocks, and the rest); every sampled unit of both groups has the
+    oracle's Vegas estimate at the same Philox points, within the bar of the test above."""
+    need_gpu()
+    prep, idx = _dbox_fused_sample(n_total=16, seed=35)
+    _, orc = feynman("double_box")
+    by = {(u.sector, u.order): u for u in orc.units}
+    integ = _integ(prep)
+    N = 20000
+    res = integ.integrate(n_iter=1, points=N, seed=14, adapt=False)
+    assert res.stats["eval_groups"] == 2 and res.stats["wide_threads"][0] > 0, res.stats
+    slots = [prep.units[i].program.n_slots for i in idx]
+    assert min(slots) <= 40 < max(slots)
+    for i in idx:
+        u = prep.units[i]
+        U = V.philox.uniforms(14, u.rng_key, 0, 0, N, u.dim)
+        X, J, _ = V.vegas_map(V.uniform_grid(u.dim), U)
+        for k in range(u.n_out):
+            o = by[(u.sector, u.order + k)]
+            m, _ = integ.iterations(i, 1, k)
+            v = o.f_numpy(X) * J
+            bound = 2 * C_SCALED * UROUND["fp64"] * np.mean(P.magnitude_numpy(o, X) * np.abs(J))
+            assert abs(m[0] - np.mean(v)) <= bound, (int(i), k, m[0], np.mean(v), bound)
+
+
 def test_mixed_units_points():
     """MixSectors programs: per point, the sum of the oracle's integrands of the sectors
     the unit mixes (box: 3 sectors per program; double box: 4, a sample of 8 units)."""

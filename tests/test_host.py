@@ -109,6 +109,20 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(_native.EXPORTS)
 
 
+def test_structure_layouts_match_the_library():
+    """Every ctypes mirror has the size of its C structure as the library was compiled
+    (host-only call, no GPU)."""
+    from paper_1511_03614_gb300 import build, _native as N
+    if not os.path.exists(build.LIB):
+        pytest.skip("library not built")
+    lib = N.load()
+    sizes = (C.c_int64 * 16)()
+    n = lib.fiesta_abi_sizes(sizes, 16)
+    assert n == len(N.ABI_STRUCTS)
+    for i, name in enumerate(N.ABI_STRUCTS):
+        assert C.sizeof(getattr(N, name)) == sizes[i], (name, C.sizeof(getattr(N, name)), sizes[i])
+
+
 def test_load_rejects_invalid_program_without_gpu():
     """The validator runs before any device call, so this works on a CPU-only host."""
     from paper_1511_03614_gb300 import build, _native as N
