@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--threads", type=int, default=256, help="kernel mode: threads per block")
     ap.add_argument("--ppt", type=int, default=8, help="kernel mode: points per thread per work item")
     ap.add_argument("--units", type=int, default=0, help="kernel mode, stress: the first N integrands (0: all)")
+    ap.add_argument("--wide-threads", type=int, default=0,
+                    help="kernel mode: split the fused units by slot count, the few-slot group at this block size")
+    ap.add_argument("--min-slots", type=int, default=0, help="kernel mode: only units with at least this many slots")
     ap.add_argument("--max-slots", type=int, default=0,
                     help="kernel mode: only the units whose programs need at most this many slots (0: all)")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre", "kernel"],
@@ -397,6 +400,7 @@ def run_ours(args):
                        "launch_shape": {"threads": res.stats.get("threads"),
                                         "points_per_thread": res.stats.get("points_per_thread"),
                                         "wide_threads": res.stats.get("wide_threads"),
+                                        "wide_points_per_thread": res.stats.get("wide_points_per_thread"),
                                         "eval_groups": res.stats.get("eval_groups")} if res else None,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)"},
@@ -732,17 +736,20 @@ def run_kernel(args):
     else:
         prep = prepared(args.workload, args.fuse)
         rng = "philox"
-    if args.max_slots:
+    if args.max_slots or args.min_slots:
         import dataclasses
-        prep = dataclasses.replace(prep, units=[u for u in prep.units if u.program.n_slots <= args.max_slots])
+        hi = args.max_slots or 1 << 30
+        prep = dataclasses.replace(prep, units=[u for u in prep.units if args.min_slots <= u.program.n_slots <= hi])
     pts = args.points or 200_000
     ig = Integrator(prep)
     for s in range(2):
         r = ig.integrate(n_iter=1, points=pts, seed=1 + s, rng=rng, adapt=2, threads=args.threads,
                          points_per_thread=args.ppt, precision=args.precision, graph=False,
+                         wide_threads=args.wide_threads,
                          accumulate="registers" if args.workload != "stress" else "auto")
     print(json.dumps({"mode": "kernel", "workload": args.workload, "precision": args.precision, "points": pts,
                       "units": len(prep.units), "threads": args.threads, "ppt": args.ppt,
+                      "wide_threads": args.wide_threads, "eval_groups": r.stats["eval_groups"],
                       "eval_ms": r.stats["eval_ms"],
                       "unit_points_per_s": r.stats["unit_points"] / (r.stats["eval_ms"] * 1e-3)}))
 

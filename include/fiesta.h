@@ -104,9 +104,10 @@ typedef struct {
     int64_t unit_begin;       /* integrate units [unit_begin, unit_end) only ... */
     int64_t unit_end;         /* ... unit_end <= 0 means all units */
     int64_t timeout_ms;       /* device time budget per kernel launch; 0 = none */
-    int32_t threads;          /* threads per block (multiple of 32, <= 256, or <= 512 for fused units with
-                                 register sums; a power of two with Sobol); 0 = autotuned, which also splits
-                                 a precision's fused units by slot count (see fiesta_stats.wide_threads) */
+    int32_t threads;          /* threads per block (multiple of 32, <= 512; <= 384 when fused units keep
+                                 their sums in shared memory; a power of two with Sobol); 0 = autotuned,
+                                 which also splits a precision's units by slot count (see
+                                 fiesta_stats.wide_threads) */
     int32_t reset_grid;       /* nonzero: start from the uniform grid (else keep the last one) */
     int32_t iter_offset;      /* added to the iteration number in the point streams */
     int32_t points_per_thread;/* points per thread per work item; 0 = autotuned */
@@ -147,7 +148,11 @@ typedef struct {
     int64_t flow_keep;        /* FLOW: points kept per unit for training (0: 4096) */
     double flow_lr;           /* FLOW: Adam learning rate (0: 2e-3) */
     int32_t flow_power;       /* FLOW: loss weights (|f|/q)^power (0: 1, the KL divergence) */
-    int32_t reserved2;
+    int32_t wide_threads;     /* > 0: split each precision's units by slot count whenever the
+                                 largest slot file does not fit a 512-thread block (as the autotuner
+                                 does) and run the units whose files fit with this many threads per
+                                 block (multiple of 32, <= 512); points_per_thread, when given, applies
+                                 to both groups.  0: split only when the shape is autotuned. */
 } fiesta_options;
 
 typedef struct {
@@ -179,9 +184,10 @@ typedef struct {
     int32_t points_per_thread[2];
     int64_t points_ext;       /* points promoted near the boundary (small_x: binary64 -> double-double,
                                  small_x32: binary32 -> binary64) */
-    int32_t wide_threads[2];  /* block size of the fused units with few slots when a precision's units
+    int32_t wide_threads[2];  /* block size of the units with few slots when a precision's units
                                  were split by slot count (their slot files fit 512-thread blocks and the
                                  others' do not); 0: not split */
+    int32_t wide_points_per_thread[2];
     int32_t eval_groups;      /* evaluation launches per iteration (one per precision and slot group) */
     int32_t pad;
 } fiesta_stats;

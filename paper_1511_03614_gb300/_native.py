@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("accumulate", C.c_int32), ("small_x", C.c_double),
                 ("unit_points", C.POINTER(C.c_int64)), ("small_x32", C.c_double), ("proposal", C.c_int32),
                 ("flow_train_steps", C.c_int32), ("flow_keep", C.c_int64), ("flow_lr", C.c_double),
-                ("flow_power", C.c_int32), ("reserved2", C.c_int32)]
+                ("flow_power", C.c_int32), ("wide_threads", C.c_int32)]
 
 
 class AccuracyOptions(C.Structure):
@@ -77,7 +77,8 @@ class Stats(C.Structure):
                 ("points_per_s", C.c_double), ("kernels_launched", C.c_int32), ("eval_launches", C.c_int32),
                 ("units_fp32", C.c_int64), ("unit_points", C.c_int64), ("threads", C.c_int32 * 2),
                 ("points_per_thread", C.c_int32 * 2), ("points_ext", C.c_int64),
-                ("wide_threads", C.c_int32 * 2), ("eval_groups", C.c_int32), ("pad", C.c_int32)]
+                ("wide_threads", C.c_int32 * 2), ("wide_points_per_thread", C.c_int32 * 2),
+                ("eval_groups", C.c_int32), ("pad", C.c_int32)]
 
 
 class CuhreOptions(C.Structure):

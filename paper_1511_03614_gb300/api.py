@@ -126,7 +126,8 @@ class Integrator:
                   alpha=1.5, skip_first=False, units=None, timeout_ms=0, threads=0, reset_grid=True,
                   iter_offset=0, assemble_result=True, raise_nonfinite=True, points_per_thread=0,
                   probe_points=0, fp32_budget=0.0, graph=True, small_x=0.0, unit_points=None, small_x32=None,
-                  accumulate="auto", proposal="vegas", flow_train_steps=0, flow_keep=0, flow_lr=0.0, flow_power=0):
+                  accumulate="auto", proposal="vegas", flow_train_steps=0, flow_keep=0, flow_lr=0.0, flow_power=0,
+                  wide_threads=0):
         lo = min(u.order for u in self.prep.units)
         hi = max(u.order + _n_orders(u) - 1 for u in self.prep.units)
         nord = hi - lo + 1
@@ -139,7 +140,7 @@ class Integrator:
                         int(points_per_thread), int(probe_points), float(fp32_budget), int(not graph),
                         {"auto": 0, "registers": 1, "shared": 2}[accumulate],
                         float(small_x), None, float(small_x32), N.PROPOSAL[proposal], int(flow_train_steps),
-                        int(flow_keep), float(flow_lr), int(flow_power), 0)
+                        int(flow_keep), float(flow_lr), int(flow_power), int(wide_threads))
         if unit_points is not None:
             upts = np.ascontiguousarray(unit_points, dtype=np.int64)
             if upts.shape != (e - b,):
@@ -166,7 +167,8 @@ class Integrator:
                      kernels_launched=st.kernels_launched, eval_launches=st.eval_launches,
                      units_fp32=st.units_fp32, unit_points=st.unit_points, threads=tuple(st.threads),
                      points_per_thread=tuple(st.points_per_thread), points_ext=st.points_ext,
-                     wide_threads=tuple(st.wide_threads), eval_groups=st.eval_groups)
+                     wide_threads=tuple(st.wide_threads), wide_points_per_thread=tuple(st.wide_points_per_thread),
+                     eval_groups=st.eval_groups)
         res = Result(values, errors, pu, stats)
         if assemble_result and units is None:
             res.assembled, res.assembled_errors = assemble_records(self.prep, *recs)

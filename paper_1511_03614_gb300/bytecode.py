@@ -131,18 +131,20 @@ def _schedule(nodes, live, outs):
         for u in touched:                  # their scores may have improved
             if u not in done and waiting[u] == 0:
                 heapq.heappush(heap, (-score(u), u))
-    # constants just before their first user
-    consts = [i for i in live if nodes[i][0] == "c"]
+    return _place_constants(nodes, live, order)
+
+
+def _place_constants(nodes, live, order):
+    """Insert the constants of ``live`` just before their first user in ``order``."""
     first_use = {}
-    pos = {i: k for k, i in enumerate(order)}
-    for i in order:
+    for k, i in enumerate(order):
         for a in _args(nodes[i]):
             if nodes[a][0] == "c" and a not in first_use:
-                first_use[a] = pos[i]
-    out = []
+                first_use[a] = k
     by_pos = {}
-    for cidx in consts:
+    for cidx in (i for i in live if nodes[i][0] == "c"):
         by_pos.setdefault(first_use.get(cidx, len(order)), []).append(cidx)
+    out = []
     for k, i in enumerate(order):
         out.extend(by_pos.get(k, []))
         out.append(i)
@@ -150,11 +152,55 @@ def _schedule(nodes, live, outs):
     return out
 
 
+def _schedule_need_first(nodes, live, outs, ties_last_first=False):
+    """Order the live nodes depth first from the results, visiting a node's operands in
+    decreasing order of the slots their own evaluation needs (the Sethi-Ullman order
+    for expression trees; on a shared operand the estimate counts it in every user, so
+    it is an upper bound, and a node is emitted once, at its first visit).  Operands of
+    equal need are visited in argument order, or last first."""
+    args = {i: [a for a in _args(nodes[i]) if nodes[a][0] != "c"] for i in live}
+    need = {}
+    for root in live:                       # post-order need labels without recursion
+        stack = [(root, False)]
+        while stack:
+            i, expanded = stack.pop()
+            if i in need or nodes[i][0] == "c":
+                continue
+            if not expanded:
+                stack.append((i, True))
+                stack.extend((a, False) for a in args[i] if a not in need)
+                continue
+            ls = sorted((need[a] for a in args[i]), reverse=True)
+            need[i] = max([1] + [l + k for k, l in enumerate(ls)])
+    order, done = [], set()
+    for root in sorted((o for o in dict.fromkeys(outs) if nodes[o][0] != "c"), key=lambda o: -need[o]):
+        stack = [(root, False)]
+        while stack:
+            i, expanded = stack.pop()
+            if i in done:
+                continue
+            if expanded:
+                done.add(i)
+                order.append(i)
+                continue
+            stack.append((i, True))
+            # pushed in reverse visiting order: the neediest operand is popped first
+            todo = [a for a in args[i] if a not in done]
+            if not ties_last_first:
+                todo.reverse()
+            for a in sorted(todo, key=lambda a: need[a]):
+                stack.append((a, False))
+    return _place_constants(nodes, live, order)
+
+
 def emit(graph, out, dim, fuse_fma=True):
     """Lower the nodes reachable from ``out`` (one node or a list of result nodes) to a
     Program (linear-scan slot allocation); results stay live to the end.  With
     ``fuse_fma`` a product used only by one sum is first contracted into a fused
-    multiply-add (``ir.contract``)."""
+    multiply-add (``ir.contract``).  The nodes are ordered three ways (greedy list
+    scheduling, and depth first in need order with either tie order) and the order
+    needing the fewest slots is kept, then the shortest: the slot file sets how many
+    threads share an SM, and every order computes each value by the same operations."""
     outs = list(out) if isinstance(out, (list, tuple)) else [out]
     nodes = graph.nodes
 
@@ -173,7 +219,25 @@ def emit(graph, out, dim, fuse_fma=True):
         from .ir import contract
         outs = contract(graph, outs)
     live = live_set(outs)
-    order = _schedule(nodes, live, outs)
+    best, err = None, None
+    schedules = (_schedule, _schedule_need_first,
+                 lambda nodes, live, outs: _schedule_need_first(nodes, live, outs, ties_last_first=True))
+    for schedule in schedules:
+        try:
+            prog = _lower(nodes, schedule(nodes, live, outs), outs, dim)
+        except OverflowError as e:          # too many slots in this order: try the other
+            err = e
+            continue
+        if best is None or (prog.n_slots, len(prog.code)) < (best.n_slots, len(best.code)):
+            best = prog
+    if best is None:
+        raise err
+    validate(best)
+    return best
+
+
+def _lower(nodes, order, outs, dim):
+    """Linear-scan slot allocation and encoding of the scheduled nodes."""
     out = outs[0]
 
     consts = []
@@ -302,7 +366,6 @@ def emit(graph, out, dim, fuse_fma=True):
         raise OverflowError("too many constants")
     prog = Program(np.array(code, dtype=np.uint32), np.array(consts, dtype=np.float64),
                    max(n_slots, 1), slot[out], dim, counts, tuple(slot[o] for o in outs))
-    validate(prog)
     return prog
 
 

@@ -107,7 +107,7 @@ def test_slot_groups_same_point_sums():
     _, orc = feynman("double_box")
     by = {(u.sector, u.order): u for u in orc.units}
     integ = _integ(prep)
-    N = 20000
+    N = 50000          # both groups hold at least 512 * 16 points per SM: the split pays
     res = integ.integrate(n_iter=1, points=N, seed=14, adapt=False)
     assert res.stats["eval_groups"] == 2 and res.stats["wide_threads"][0] > 0, res.stats
     slots = [prep.units[i].program.n_slots for i in idx]
