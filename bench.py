@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=256, help="kernel mode: threads per block")
     ap.add_argument("--ppt", type=int, default=8, help="kernel mode: points per thread per work item")
     ap.add_argument("--units", type=int, default=0, help="kernel mode, stress: the first N integrands (0: all)")
+    ap.add_argument("--launch-shape", default="",
+                    help="throughput mode: threads,points_per_thread,wide_threads instead of the autotuner's")
     ap.add_argument("--wide-threads", type=int, default=0,
                     help="kernel mode: split the fused units by slot count, the few-slot group at this block size")
     ap.add_argument("--min-slots", type=int, default=0, help="kernel mode: only units with at least this many slots")
@@ -301,6 +303,9 @@ def run_ours(args):
     # every row of the path: points, map, evaluation, reduction, refinement, assembly
     kw = dict(n_iter=iters, points=pts, seed=1 + rank, rng=rng, precision=args.precision,
               adapt=2 if iters == 1 else True)
+    if args.launch_shape:               # pin the autotuner's choice (e.g. for a profiler run)
+        t, q, w = (int(v) for v in args.launch_shape.split(","))
+        kw.update(threads=t, points_per_thread=q, wide_threads=w)
     for _ in range(args.warmup):
         integ.integrate(**kw)
     torch.cuda.synchronize()
