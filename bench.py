@@ -226,10 +226,11 @@ def op_costs32(peaks):
 # memory, so this does not grow with the number of points.  None: not captured for
 # the current kernel.
 TRAFFIC = {("double_box", "fp64", True): (
-    3988992, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_eval<double, Philox, 6, registers> launch "
-             "on the fused double box at 2e5 points per unit (bench.py --mode kernel --workload double_box --points "
-             "200000 --threads 256 --ppt 8); programs, constants and grids stay L2-resident across block visits, so "
-             "the DRAM bytes do not grow with the points per unit")}
+    41250560 + 40871936 + 1612544,
+    "ncu dram__bytes_read.sum + dram__bytes_write.sum of the two k_eval<double, Philox, 6, registers> launches of "
+    "one evaluation pass at the bench's size and shapes (bench.py --mode kernel --workload double_box --points "
+    "10000000 --threads 384 --ppt 8 --wide-threads 384): mostly the (unit, chunk) partial sums of the fixed-order "
+    "reduction, written back once they outgrow L2, and the sector fills of those 48-byte records")}
 
 
 def roofline_of(prep, res, peaks, pts, pass_s, args, iters):
