@@ -67,7 +67,7 @@ extern "C" {
 typedef struct {
     int32_t dim;          /* integration dimension, 1..FIESTA_MAX_DIM */
     int32_t n_instr;      /* number of instruction words, >= 1 */
-    int32_t n_const;      /* number of constants, >= 0 */
+    int32_t n_const;      /* number of constants, 0..49152 */
     int32_t n_slots;      /* register-file size, 1..255 */
     int32_t out_slot;     /* slot holding the integrand value at the end */
     int32_t order;        /* power of eps of this unit (used for the per-order sums) */
@@ -545,6 +545,21 @@ int fiesta_flow_check(fiesta_ctx *ctx, int64_t unit, int64_t n, int32_t precisio
 void fiesta_free(fiesta_ctx *ctx);
 const char *fiesta_last_error(void);
 int fiesta_version(void);
+
+/* The forwarded program the evaluation kernels execute for one program, for checking
+ * on the host (no counterpart in the method; host only, no device call).  The program is
+ * validated as fiesta_load_sectors does.  Each 64-bit word is one executed instruction:
+ * bits 0-7 the opcode, 8-15 the destination slot, 16-31, 32-47 and 48-63 the operand
+ * references X, Y, Z.  For ADD, SUB, MUL, NEG, MAC, ADDC, MULC, MACC and MOV the
+ * instruction computes fma(X, Y, Z).  For DIV, POWI, LOG, INV and ATAN2, X and Y are the
+ * first and second operand; for POWI, Y is the exponent byte.  A reference below 0xC000
+ * is a constant index; 0xC000 + s is slot s; 0xD000 + j is coordinate j; 0xE000 + k is
+ * the fixed constant -0, 1 or -1 (k = 0, 1, 2).  LDX and LDC execute nothing: their
+ * readers name the coordinate or constant.  A MOV into the slot the next instruction
+ * writes is folded into that instruction.  out (host, caller-owned) receives the first
+ * min(count, cap) words.  Returns the word count, which is at most n_instr, or
+ * FIESTA_E_INVALID. */
+int64_t fiesta_micro_ops(const fiesta_program *prog, uint64_t *out, int64_t cap);
 
 /* Sizes in bytes of this header's structures as the library was compiled, for a binding
  * to check its own layouts against (no counterpart in the method; host only, no device

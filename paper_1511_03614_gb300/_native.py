@@ -142,6 +142,7 @@ EXPORTS = {
     "fiesta_last_error": (C.c_char_p, []),
     "fiesta_version": (C.c_int, []),
     "fiesta_abi_sizes": (C.c_int, [C.POINTER(C.c_int64), C.c_int32]),
+    "fiesta_micro_ops": (C.c_int64, [C.c_void_p, C.POINTER(C.c_uint64), C.c_int64]),
 }
 
 # the ctypes mirrors in the order fiesta_abi_sizes reports the C structures
