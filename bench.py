@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--min-slots", type=int, default=0, help="kernel mode: only units with at least this many slots")
     ap.add_argument("--max-slots", type=int, default=0,
                     help="kernel mode: only the units whose programs need at most this many slots (0: all)")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre", "kernel"],
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "tta", "cuhre", "kernel", "flow"],
                     help="tta: GPU-seconds to 1e-4 relative error per eps order, each precision policy")
     ap.add_argument("--target", type=float, default=1e-4)
     ap.add_argument("--max-iters", type=int, default=400, help="tta mode: Vegas iteration cap per form")
@@ -760,6 +760,56 @@ def run_kernel(args):
                       "unit_points_per_s": r.stats["unit_points"] / (r.stats["eval_ms"] * 1e-3)}))
 
 
+# multiply-adds of one training point (4 coupling layers, MLP 16 -> 64 -> 64 -> 16): the
+# forward pass, the reverse pass's recomputation, the three reverse products
+# (dH2 = dout W3^T, dH1 = dH2 W2^T, d(input) = dH1 W1^T) and the three weight-gradient
+# products (dW3 = H2^T dout, dW2 = H1^T dH2, dW1 = In^T dH1)
+FLOW_LAYER_MACS = 16 * 64 + 64 * 64 + 64 * 16
+FLOW_TRAIN_FLOPS_PER_POINT = 2 * 4 * (1 + 1 + 1 + 1) * FLOW_LAYER_MACS     # 196 608
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (cuBLAS, burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16"
+
+
+def run_flow_kernels(args):
+    """The learned proposal's kernels on the workload's fused units (one flow per
+    sector): per step one sampling pass of --points points per sector that keeps 4096
+    training points per sector, then 20 Adam steps of tensor-core training on them.
+    Reports device time per pass and per training step, and the training kernel's
+    tensor roofline (algorithmic BF16 flops of the MLP products over the measured
+    cuBLAS BF16 peak).  Not the headline line."""
+    import torch
+    from paper_1511_03614_gb300 import Integrator
+    torch.cuda.set_device(0)
+    prep = prepared(args.workload, fuse=True)
+    integ = Integrator(prep)
+    integ.flow_init(seed=3)
+    pts, keep, tsteps = args.points or 200_000, 4096, 20
+    sample_ms, train_ms = [], []
+    for s in range(args.warmup + args.steps):
+        _, _, st = integ.flow_sample(pts, seed=1, iteration=s, keep=keep)
+        _, tt = integ.flow_train(tsteps, lr=2e-3, power=1)
+        if s >= args.warmup:
+            sample_ms.append(st["gpu_ms"])
+            train_ms.append(tt["gpu_ms"])
+    nu = len(prep.units)
+    step_s = statistics.median(train_ms) * 1e-3 / tsteps
+    achieved = nu * keep * FLOW_TRAIN_FLOPS_PER_POINT / step_s * 1e-12
+    peak, src = _bf16_peak()
+    print(json.dumps({"mode": "flow", "workload": args.workload, "units": nu, "points_per_unit": pts,
+                      "keep_per_unit": keep, "sample_ms_per_pass": statistics.median(sample_ms),
+                      "sample_points_per_s": nu * pts / (statistics.median(sample_ms) * 1e-3),
+                      "train_ms_per_adam_step": step_s * 1e3,
+                      "train_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                         "frac": achieved / peak, "peak_source": src,
+                                         "work": f"{FLOW_TRAIN_FLOPS_PER_POINT} BF16 flops per training point"}}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -770,6 +820,8 @@ def main():
         run_tta(args)
     elif args.mode == "cuhre":
         run_cuhre(args)
+    elif args.mode == "flow":
+        run_flow_kernels(args)
     else:
         run_ours(args)
 

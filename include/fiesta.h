@@ -503,8 +503,10 @@ int fiesta_sample_noalloc(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end,
  * Learned proposal (not in the paper): per unit, a normalising flow over the
  * unit cube that stands in for the Vegas map.  Four affine coupling layers in
  * logit space, each with an MLP 16 -> 64 -> 64 -> 16 (ReLU); the sampler runs
- * the MLPs on the tensor cores in BF16 with FP32 accumulation; training runs
- * in binary32 with Adam.  Parameters: FIESTA_FLOW_PARAMS floats per unit, per
+ * the MLPs on the tensor cores in BF16 with FP32 accumulation; training
+ * computes the gradient on the tensor cores too (forward and reverse-mode
+ * products of the MLPs as BF16 MMAs with FP32 accumulation) and updates
+ * binary32 master weights with Adam.  Parameters: FIESTA_FLOW_PARAMS floats per unit, per
  * layer W1[16][64], b1[64], W2[64][64], b2[64], W3[64][16] (outputs 0..7 the
  * scales, 8..15 the shifts), b3[16].
  *
@@ -527,8 +529,9 @@ int fiesta_sample_noalloc(fiesta_ctx *ctx, int64_t unit_begin, int64_t unit_end,
  *   last step's loss per unit.
  * fiesta_flow_check: parity hook for one unit: the sampler at the caller's base
  *   points z (n x dim, host) gives x, log q and f; the training pass at those x
- *   with the caller's weights w gives log q (binary32), the loss and its
- *   gradient (FIESTA_FLOW_PARAMS floats).  All arrays host.
+ *   with the caller's weights w gives log q, the loss and its gradient
+ *   (FIESTA_FLOW_PARAMS floats), computed as fiesta_flow_train computes them.
+ *   All arrays host.
  * Errors: FIESTA_E_INVALID, FIESTA_E_NOMEM, FIESTA_E_CUDA, FIESTA_E_NONFINITE.
  */
 #define FIESTA_FLOW_PARAMS 25152

@@ -15,9 +15,11 @@
 //   the C fragment of the last, so s and t arrive in the lane that applies them,
 //   and each layer's C fragments are the next layer's A fragments.  Then every
 //   lane evaluates its own point with the bytecode interpreter.
-// k_flow_train: one thread per training point, binary32: normalising pass,
-//   reverse-mode gradient of L = -sum_i w_i log q(x_i), weight gradients summed
-//   over each warp's 32 points in shared memory before the global atomics.
+// k_flow_train_tc: the gradient of L = -sum_i w_i log q(x_i) on the tensor cores:
+//   one warp per 16 training points, forward pass, then per layer the MLP's
+//   reverse mode as MMAs (BF16 operands, binary32 accumulation), the weight
+//   gradients with the points as the MMA's K dimension (movmatrix transposes),
+//   summed per block in shared memory.
 // k_flow_adam: Adam update of the binary32 master weights; k_flow_pack: the
 //   BF16 transposed copies the sampler reads.
 
@@ -67,8 +69,13 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
 // MLP of one layer for one 16-point tile.  in0/in1: this lane's two input
 // coordinates (2t, 2t+1) of rows g and g+8 (already masked); out: raw_s and t of
 // this lane's coordinates for rows g (o[0..1] s, o[2..3] t) and g+8 (o[4..7]).
-__device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ lay, float in_g0, float in_g1,
-                                            float in_h0, float in_h1, float (&o)[8]) {
+// H1, H2: the two hidden activations after the ReLU, rounded to BF16, as the A
+// fragments of the next MMA (k-tile kt: [0] row g, columns 16kt + 2t, +1; [1] row
+// g + 8; [2], [3] the same rows at columns 16kt + 8 + 2t, +1); the training kernel
+// keeps them for the reverse pass.
+__device__ __forceinline__ void fl_mlp_tile_keep(const unsigned char *__restrict__ lay, float in_g0, float in_g1,
+                                                 float in_h0, float in_h1, uint32_t (&A)[4][4], uint32_t (&A2)[4][4],
+                                                 float (&o)[8]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const __nv_bfloat16 *W1t = reinterpret_cast<const __nv_bfloat16 *>(lay) + FLP_W1;
     const __nv_bfloat16 *W2t = reinterpret_cast<const __nv_bfloat16 *>(lay) + FLP_W2;
@@ -77,7 +84,6 @@ __device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ la
     const float *b1 = bias, *b2 = bias + FL_HID, *b3 = bias + 2 * FL_HID;
     // layer 1: K = 16 (inputs 8..15 are zero), N = 64
     const uint32_t a0 = pack_bf16(in_g0, in_g1), a1 = pack_bf16(in_h0, in_h1);
-    uint32_t A[4][4];                       // next layer's A fragments, k-tiles 0..3
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
@@ -90,7 +96,6 @@ __device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ la
         A[nt >> 1][(nt & 1) * 2 + 1] = r1;
     }
     // layer 2: K = 64, N = 64
-    uint32_t A2[4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
@@ -120,6 +125,12 @@ __device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ la
         o[4 + nt * 2 + 0] = c[2] + bx;
         o[4 + nt * 2 + 1] = c[3] + by;
     }
+}
+
+__device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ lay, float in_g0, float in_g1,
+                                            float in_h0, float in_h1, float (&o)[8]) {
+    uint32_t A[4][4], A2[4][4];
+    fl_mlp_tile_keep(lay, in_g0, in_g1, in_h0, in_h1, A, A2, o);
 }
 
 struct FlowSampleParams {
@@ -352,226 +363,6 @@ struct FlowTrainParams {
     int power;
 };
 
-// Sum over the 32 points of a warp of u_i (x) v_i (outer products, U: [32][nu],
-// V: [32][nv] in shared memory), added into G[nu][nv] with one atomic per entry.
-__device__ __forceinline__ void warp_outer_add(const float *U, int nu_, int su, const float *V, int nv, int sv_,
-                                               float *G) {
-    const int lane = threadIdx.x & 31;
-    for (int e = lane; e < nu_ * nv; e += 32) {
-        const int i = e / nv, j = e % nv;
-        float acc = 0.f;
-#pragma unroll 8
-        for (int s = 0; s < 32; ++s) acc = fmaf(U[s * su + i], V[s * sv_ + j], acc);
-        if (acc != 0.f) atomicAdd(G + i * nv + j, acc);
-    }
-}
-
-__global__ void __launch_bounds__(FL_THREADS) k_flow_train(FlowTrainParams p) {
-    extern __shared__ __align__(16) float fsm[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t pos = blockIdx.x / p.blocks_per_unit, unit = p.unit_begin + pos;
-    const int64_t blk = blockIdx.x % p.blocks_per_unit;
-    const int d = p.units[unit].dim;
-    float *W = fsm;                                         // FL_PARAMS master weights
-    float *stage = fsm + FL_PARAMS + warp * (32 * (FL_HID + FL_HID));
-    float *SU = stage, *SV = stage + 32 * FL_HID;           // [32][64] each
-    __shared__ double s_loss[FL_THREADS];
-    for (int i = tid; i < FL_PARAMS; i += blockDim.x) W[i] = p.params[unit * FL_PARAMS + i];
-    __syncthreads();
-    float *G = p.grad + unit * FL_PARAMS;
-    const int64_t per_block = (p.keep + p.blocks_per_unit - 1) / p.blocks_per_unit;
-    const int64_t first = blk * per_block, last = min(p.keep, first + per_block);
-    double loss = 0.0;
-    // every warp runs whole rounds of 32 points so that shuffles and staging stay uniform
-    for (int64_t base = first; base < last; base += blockDim.x) {
-        const int64_t i = base + tid;
-        const bool valid = i < last;
-        float a[MAXD], al[FL_L][MAXD];
-        float w = 0.f;
-        if (valid) {
-            const int64_t row = (p.buf_unit0 + pos) * p.keep + i;
-            for (int j = 0; j < MAXD; ++j) a[j] = p.tr_x[row * MAXD + j];
-            if (p.w_in) {
-                w = static_cast<float>(p.w_in[i]);
-            } else {
-                const double r = fabs(static_cast<double>(p.tr_f[row])) * exp(-static_cast<double>(p.tr_lq[row]));
-                const double ww = (p.power == 2 ? r * r : r) / p.wsum[pos];
-                w = isfinite(ww) ? static_cast<float>(ww) : 0.f;
-            }
-        } else {
-            for (int j = 0; j < MAXD; ++j) a[j] = 0.f;
-        }
-        float lq = 0.f;
-        bool finite = true;
-#pragma unroll
-        for (int j = 0; j < MAXD; ++j) {
-            finite = finite && isfinite(a[j]);
-            if (j < d) lq += softplusf(-a[j]) + softplusf(a[j]);            // -log x - log(1 - x)
-        }
-        if (!finite) {                                                       // skip such a point
-            w = 0.f;
-            for (int j = 0; j < MAXD; ++j) a[j] = 0.f;
-            lq = 0.f;
-        }
-        // normalising pass, keeping each layer's input
-        for (int l = 0; l < FL_L; ++l) {
-            const float *P = W + l * FL_PER_LAYER;
-#pragma unroll
-            for (int j = 0; j < MAXD; ++j) al[l][j] = a[j];
-            float in[MAXD];
-#pragma unroll
-            for (int j = 0; j < MAXD; ++j) in[j] = (j < d && fl_in_A(l, j, d)) ? a[j] : 0.f;
-            float h1[FL_HID];
-            for (int n = 0; n < FL_HID; ++n) {
-                float acc = P[FL_B1 + n];
-#pragma unroll
-                for (int k = 0; k < MAXD; ++k) acc = fmaf(in[k], P[FL_W1 + k * FL_HID + n], acc);
-                h1[n] = fmaxf(acc, 0.f);
-            }
-            float outv[FL_OUT];
-#pragma unroll
-            for (int q = 0; q < FL_OUT; ++q) outv[q] = P[FL_B3 + q];
-            for (int n = 0; n < FL_HID; ++n) {
-                float acc = P[FL_B2 + n];
-                for (int k = 0; k < FL_HID; ++k) acc = fmaf(h1[k], P[FL_W2 + k * FL_HID + n], acc);
-                const float h2 = fmaxf(acc, 0.f);
-#pragma unroll
-                for (int q = 0; q < FL_OUT; ++q) outv[q] = fmaf(h2, P[FL_W3 + n * FL_OUT + q], outv[q]);
-            }
-#pragma unroll
-            for (int j = 0; j < MAXD; ++j) {
-                if (j < d && !fl_in_A(l, j, d)) {
-                    const float s = FL_S * tanhf(outv[j] / FL_S);
-                    a[j] = a[j] * __expf(s) + outv[8 + j];
-                    lq += s;
-                }
-            }
-        }
-        float gsum[MAXD];
-#pragma unroll
-        for (int j = 0; j < MAXD; ++j) {
-            if (j < d) {
-                lq += -softplusf(-a[j]) - softplusf(a[j]);                     // log z + log(1 - z)
-                const float sg = 1.f / (1.f + __expf(-a[j]));
-                gsum[j] = -w * (1.f - 2.f * sg);
-            } else {
-                gsum[j] = 0.f;
-            }
-        }
-        if (valid) {
-            loss += -static_cast<double>(w) * lq;
-            if (p.lq_out) p.lq_out[i] = lq;
-        }
-        const float c = -w;
-        // reverse pass
-        for (int l = FL_L - 1; l >= 0; --l) {
-            const float *P = W + l * FL_PER_LAYER;
-            float *GL = G + l * FL_PER_LAYER;
-            float in[MAXD];
-#pragma unroll
-            for (int j = 0; j < MAXD; ++j) in[j] = (j < d && fl_in_A(l, j, d)) ? al[l][j] : 0.f;
-            // recompute the MLP
-            float h1[FL_HID], h2p[FL_HID];
-            for (int n = 0; n < FL_HID; ++n) {
-                float acc = P[FL_B1 + n];
-#pragma unroll
-                for (int k = 0; k < MAXD; ++k) acc = fmaf(in[k], P[FL_W1 + k * FL_HID + n], acc);
-                h1[n] = fmaxf(acc, 0.f);
-            }
-            float outv[FL_OUT];
-#pragma unroll
-            for (int q = 0; q < FL_OUT; ++q) outv[q] = P[FL_B3 + q];
-            for (int n = 0; n < FL_HID; ++n) {
-                float acc = P[FL_B2 + n];
-                for (int k = 0; k < FL_HID; ++k) acc = fmaf(h1[k], P[FL_W2 + k * FL_HID + n], acc);
-                h2p[n] = acc;
-                const float h2 = fmaxf(acc, 0.f);
-#pragma unroll
-                for (int q = 0; q < FL_OUT; ++q) outv[q] = fmaf(h2, P[FL_W3 + n * FL_OUT + q], outv[q]);
-            }
-            float dout[FL_OUT];
-#pragma unroll
-            for (int j = 0; j < MAXD; ++j) {
-                dout[j] = 0.f;
-                dout[8 + j] = 0.f;
-                if (j < d && !fl_in_A(l, j, d)) {
-                    const float th = tanhf(outv[j] / FL_S);
-                    const float s = FL_S * th;
-                    const float es = __expf(s);
-                    const float ds = gsum[j] * al[l][j] * es + c;
-                    dout[j] = ds * (1.f - th * th);
-                    dout[8 + j] = gsum[j];
-                    gsum[j] = gsum[j] * es;
-                }
-            }
-            // W3, b3: stage h2 and dout
-            for (int k = 0; k < FL_HID; ++k) SU[lane * FL_HID + k] = fmaxf(h2p[k], 0.f);
-            for (int q = 0; q < FL_OUT; ++q) SV[lane * FL_HID + q] = dout[q];
-            __syncwarp();
-            warp_outer_add(SU, FL_HID, FL_HID, SV, FL_OUT, FL_HID, GL + FL_W3);
-            if (lane < FL_OUT) {
-                float acc = 0.f;
-                for (int s = 0; s < 32; ++s) acc += SV[s * FL_HID + lane];
-                if (acc != 0.f) atomicAdd(GL + FL_B3 + lane, acc);
-            }
-            __syncwarp();
-            // dh2 = W3 dout masked by the ReLU; stage h1 and dh2
-            float dh2[FL_HID];
-            for (int k = 0; k < FL_HID; ++k) {
-                float acc = 0.f;
-#pragma unroll
-                for (int q = 0; q < FL_OUT; ++q) acc = fmaf(P[FL_W3 + k * FL_OUT + q], dout[q], acc);
-                dh2[k] = h2p[k] > 0.f ? acc : 0.f;
-            }
-            for (int k = 0; k < FL_HID; ++k) {
-                SU[lane * FL_HID + k] = h1[k];
-                SV[lane * FL_HID + k] = dh2[k];
-            }
-            __syncwarp();
-            warp_outer_add(SU, FL_HID, FL_HID, SV, FL_HID, FL_HID, GL + FL_W2);
-            for (int n = lane; n < FL_HID; n += 32) {
-                float acc = 0.f;
-                for (int s = 0; s < 32; ++s) acc += SV[s * FL_HID + n];
-                if (acc != 0.f) atomicAdd(GL + FL_B2 + n, acc);
-            }
-            __syncwarp();
-            // dh1 = W2 dh2 masked by the ReLU; stage input and dh1
-            float dh1[FL_HID];
-            for (int k = 0; k < FL_HID; ++k) {
-                float acc = 0.f;
-                for (int n = 0; n < FL_HID; ++n) acc = fmaf(P[FL_W2 + k * FL_HID + n], dh2[n], acc);
-                dh1[k] = h1[k] > 0.f ? acc : 0.f;
-            }
-            for (int k = 0; k < MAXD; ++k) SU[lane * FL_HID + k] = in[k];
-            for (int k = 0; k < FL_HID; ++k) SV[lane * FL_HID + k] = dh1[k];
-            __syncwarp();
-            warp_outer_add(SU, MAXD, FL_HID, SV, FL_HID, FL_HID, GL + FL_W1);
-            for (int n = lane; n < FL_HID; n += 32) {
-                float acc = 0.f;
-                for (int s = 0; s < 32; ++s) acc += SV[s * FL_HID + n];
-                if (acc != 0.f) atomicAdd(GL + FL_B1 + n, acc);
-            }
-            __syncwarp();
-            // gradient reaching the conditioning coordinates
-#pragma unroll
-            for (int j = 0; j < MAXD; ++j) {
-                if (j < d && fl_in_A(l, j, d)) {
-                    float acc = 0.f;
-                    for (int n = 0; n < FL_HID; ++n) acc = fmaf(P[FL_W1 + j * FL_HID + n], dh1[n], acc);
-                    gsum[j] += acc;
-                }
-            }
-        }
-    }
-    s_loss[tid] = loss;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (tid < o) s_loss[tid] += s_loss[tid + o];
-        __syncthreads();
-    }
-    if (tid == 0) atomicAdd(p.loss + pos, s_loss[0]);
-}
-
 __global__ void k_flow_adam(float *params, const float *grad, float *m, float *v, int64_t n, float lr, float b1,
                             float b2, float eps, float c1, float c2) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -584,29 +375,393 @@ __global__ void k_flow_adam(float *params, const float *grad, float *m, float *v
     params[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// one layer's binary32 master weights -> the packed inference layout (BF16 transposed
+// weights + binary32 biases), by the threads of a block
+__device__ __forceinline__ void fl_pack_layer(const float *__restrict__ PL, unsigned char *dst) {
+    __nv_bfloat16 *h = reinterpret_cast<__nv_bfloat16 *>(dst);
+    float *b = reinterpret_cast<float *>(dst + FLP_HALVES * 2);
+    for (int e = threadIdx.x; e < FL_HID * FLP_S1; e += blockDim.x) {    // W1t[n][k] = W1[k][n]
+        const int n = e / FLP_S1, k = e % FLP_S1;
+        h[FLP_W1 + e] = __float2bfloat16_rn(k < FL_IN ? PL[FL_W1 + k * FL_HID + n] : 0.f);
+    }
+    for (int e = threadIdx.x; e < FL_HID * FLP_S2; e += blockDim.x) {
+        const int n = e / FLP_S2, k = e % FLP_S2;
+        h[FLP_W2 + e] = __float2bfloat16_rn(k < FL_HID ? PL[FL_W2 + k * FL_HID + n] : 0.f);
+    }
+    for (int e = threadIdx.x; e < FL_OUT * FLP_S2; e += blockDim.x) {    // W3t[n][k] = W3[k][n]
+        const int n = e / FLP_S2, k = e % FLP_S2;
+        h[FLP_W3 + e] = __float2bfloat16_rn(k < FL_HID ? PL[FL_W3 + k * FL_OUT + n] : 0.f);
+    }
+    for (int e = threadIdx.x; e < FLP_BIAS; e += blockDim.x)
+        b[e] = e < FL_HID ? PL[FL_B1 + e] : (e < 2 * FL_HID ? PL[FL_B2 + e - FL_HID] : PL[FL_B3 + e - 2 * FL_HID]);
+}
+
 // binary32 master -> packed BF16 transposed weights + binary32 biases
 __global__ void k_flow_pack(const float *params, unsigned char *packed, int64_t unit_begin) {
     const int64_t unit = unit_begin + blockIdx.x;
     const float *P = params + unit * FL_PARAMS;
     unsigned char *dst = packed + unit * FLP_UNIT_BYTES;
+    for (int l = 0; l < FL_L; ++l) fl_pack_layer(P + l * FL_PER_LAYER, dst + l * FLP_LAYER_BYTES);
+}
+
+// ---------------------------------------------------------------------------
+// Training on the tensor cores.
+//
+// k_flow_train_tc computes the loss L = -sum_i w_i log q(x_i) and its gradient by
+// reverse mode, with every dense product of the MLP on mma.sync.m16n8k16 (BF16
+// operands, binary32 accumulation) and the coupling arithmetic in binary32.  One warp takes 16
+// training points at a time, in the fragment layout of k_flow_sample: lane
+// (g, t) owns coordinates 2t, 2t+1 of points g and g + 8.  Per 16-point tile:
+//   forward, layer by layer, keeping each layer's input;
+//   reverse, layer by layer: recompute the layer's MLP (hidden activations kept as
+//     BF16 A fragments), then
+//       dH2 = (dout W3^T) masked by H2 > 0,   dH1 = (dH2 W2^T) masked by H1 > 0,
+//       d(input) = dH1 W1^T                                    (MMA, K = 16 / 64)
+//       dW3 = H2^T dout,  dW2 = H1^T dH2,  dW1 = In^T dH1      (MMA, K = the 16 points)
+//     with the point-major fragments turned into the K = points operands by
+//     movmatrix (8x8 transposes in registers); the bias gradients are the same
+//     products with an all-ones operand (db1 rides in dW1's spare input row 8).
+// The weight gradients of the block accumulate in shared memory (binary32) and are
+// added to the unit's gradient once per block.  Rounding: the MMA operands (layer
+// inputs, weights, hidden activations, dout, dH2, dH1) are BF16; the ReLU masks
+// are taken on the BF16 activations.
+// ---------------------------------------------------------------------------
+
+// reverse-pass weight copies per layer (BF16, untransposed, rows padded like the
+// inference copy): W1n[8][S2] (input rows 0..7; inputs 8..15 are always zero),
+// W2n[64][S2], W3n[64][S1]
+constexpr int FLB_W1 = 0, FLB_W2 = FLB_W1 + MAXD * FLP_S2, FLB_W3 = FLB_W2 + FL_HID * FLP_S2,
+              FLB_HALVES = FLB_W3 + FL_HID * FLP_S1;                 // 6720 bf16 per layer
+// the block's gradient accumulators per layer (binary32), rows padded so that the
+// eight row groups of an MMA result fragment fall in distinct bank pairs:
+// GW1[8][S2] (input rows 0..7), GW2[64][S2], GW3[64][S1], then gb1[64], gb2[64], gb3[16]
+constexpr int FLG_W1 = 0, FLG_W2 = FLG_W1 + MAXD * FLP_S2, FLG_W3 = FLG_W2 + FL_HID * FLP_S2,
+              FLG_B1 = FLG_W3 + FL_HID * FLP_S1, FLG_B2 = FLG_B1 + FL_HID, FLG_B3 = FLG_B2 + FL_HID,
+              FLG_LAYER = FLG_B3 + FL_OUT;                           // 6864 floats per layer
+constexpr int FLT_THREADS = 256;
+constexpr size_t FLT_SMEM = FLP_UNIT_BYTES + FL_L * FLB_HALVES * 2 + FL_L * FLG_LAYER * sizeof(float);   // 224 256 B
+static_assert(FLP_S1 % 32 == 24 && FLP_S2 % 32 == 8, "padded strides keep the gradient atomics conflict-free");
+static_assert(MAXD == 8, "the training tile maps coordinates 2t, 2t+1 of four lanes onto eight dimensions");
+
+// transpose of an 8x8 BF16 matrix held as one pair per lane (row lane/4, columns 2(lane%4), +1)
+__device__ __forceinline__ uint32_t mov_t(uint32_t x) {
+    uint32_t y;
+    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;\n" : "=r"(y) : "r"(x));
+    return y;
+}
+
+// the two halves of a BF16 pair masked by the ReLU of another pair (kept where that value is > 0)
+__device__ __forceinline__ uint32_t relu_mask_pack(float lo, float hi, uint32_t act) {
+    return pack_bf16((act & 0x7fffu) ? lo : 0.f, (act & 0x7fff0000u) ? hi : 0.f);
+}
+
+__device__ __forceinline__ void sadd(float *a, float v) {
+    if (v != 0.f) atomicAdd(a, v);
+}
+
+// adds (lo, hi) to a[0], a[1]; row groups g >= 4 take the two in the other order, so
+// that with row strides of 8 or 24 words (mod 32) every shared-memory atomic of the
+// warp lands in its own bank
+__device__ __forceinline__ void sadd_pair(float *a, float lo, float hi, bool swap) {
+    atomicAdd(swap ? a + 1 : a, swap ? hi : lo);
+    atomicAdd(swap ? a : a + 1, swap ? lo : hi);
+}
+
+__global__ void __launch_bounds__(FLT_THREADS, 1) k_flow_train_tc(FlowTrainParams p) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    unsigned char *s_fwd = tsm;
+    __nv_bfloat16 *s_bwd = reinterpret_cast<__nv_bfloat16 *>(tsm + FLP_UNIT_BYTES);
+    float *s_g = reinterpret_cast<float *>(tsm + FLP_UNIT_BYTES + FL_L * FLB_HALVES * 2);   // [layer][FLG_LAYER]
+    __shared__ double s_loss[FLT_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t pos = blockIdx.x / p.blocks_per_unit, unit = p.unit_begin + pos;
+    const int64_t blk = blockIdx.x % p.blocks_per_unit;
+    const int d = p.units[unit].dim;
+    const float *P = p.params + unit * FL_PARAMS;
     for (int l = 0; l < FL_L; ++l) {
         const float *PL = P + l * FL_PER_LAYER;
-        __nv_bfloat16 *h = reinterpret_cast<__nv_bfloat16 *>(dst + l * FLP_LAYER_BYTES);
-        float *b = reinterpret_cast<float *>(dst + l * FLP_LAYER_BYTES + FLP_HALVES * 2);
-        for (int e = threadIdx.x; e < FL_HID * FLP_S1; e += blockDim.x) {    // W1t[n][k] = W1[k][n]
-            const int n = e / FLP_S1, k = e % FLP_S1;
-            h[FLP_W1 + e] = __float2bfloat16_rn(k < FL_IN ? PL[FL_W1 + k * FL_HID + n] : 0.f);
+        fl_pack_layer(PL, s_fwd + l * FLP_LAYER_BYTES);
+        __nv_bfloat16 *B = s_bwd + l * FLB_HALVES;
+        for (int e = tid; e < MAXD * FLP_S2; e += blockDim.x) {
+            const int j = e / FLP_S2, k = e % FLP_S2;
+            B[FLB_W1 + e] = __float2bfloat16_rn(k < FL_HID ? PL[FL_W1 + j * FL_HID + k] : 0.f);
         }
-        for (int e = threadIdx.x; e < FL_HID * FLP_S2; e += blockDim.x) {
-            const int n = e / FLP_S2, k = e % FLP_S2;
-            h[FLP_W2 + e] = __float2bfloat16_rn(k < FL_HID ? PL[FL_W2 + k * FL_HID + n] : 0.f);
+        for (int e = tid; e < FL_HID * FLP_S2; e += blockDim.x) {
+            const int j = e / FLP_S2, k = e % FLP_S2;
+            B[FLB_W2 + e] = __float2bfloat16_rn(k < FL_HID ? PL[FL_W2 + j * FL_HID + k] : 0.f);
         }
-        for (int e = threadIdx.x; e < FL_OUT * FLP_S2; e += blockDim.x) {    // W3t[n][k] = W3[k][n]
-            const int n = e / FLP_S2, k = e % FLP_S2;
-            h[FLP_W3 + e] = __float2bfloat16_rn(k < FL_HID ? PL[FL_W3 + k * FL_OUT + n] : 0.f);
+        for (int e = tid; e < FL_HID * FLP_S1; e += blockDim.x) {
+            const int j = e / FLP_S1, k = e % FLP_S1;
+            B[FLB_W3 + e] = __float2bfloat16_rn(k < FL_OUT ? PL[FL_W3 + j * FL_OUT + k] : 0.f);
         }
-        for (int e = threadIdx.x; e < FLP_BIAS; e += blockDim.x)
-            b[e] = e < FL_HID ? PL[FL_B1 + e] : (e < 2 * FL_HID ? PL[FL_B2 + e - FL_HID] : PL[FL_B3 + e - 2 * FL_HID]);
+    }
+    for (int i = tid; i < FL_L * FLG_LAYER; i += blockDim.x) s_g[i] = 0.f;
+    __syncthreads();
+
+    const uint32_t ONE2 = pack_bf16(1.f, 1.f);
+    const bool swap = g >= 4;
+    const int64_t per_block = (p.keep + p.blocks_per_unit - 1) / p.blocks_per_unit;
+    const int64_t first = blk * per_block, last = min(p.keep, first + per_block);
+    const int64_t ntiles = last > first ? (last - first + 15) / 16 : 0;
+    double loss = 0.0;
+    for (int64_t tile = warp; tile < ntiles; tile += nw) {
+        const int64_t rbase = first + tile * 16;
+        float a[2][2], al[FL_L][2][2], w[2], lq[2];
+        bool valid[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int64_t i = rbase + g + 8 * r;
+            valid[r] = i < last;
+            a[r][0] = a[r][1] = 0.f;
+            w[r] = 0.f;
+            if (valid[r]) {
+                const int64_t row = (p.buf_unit0 + pos) * p.keep + i;
+                a[r][0] = p.tr_x[row * MAXD + 2 * t];
+                a[r][1] = p.tr_x[row * MAXD + 2 * t + 1];
+                if (p.w_in) {
+                    w[r] = static_cast<float>(p.w_in[i]);
+                } else {
+                    const double rr = fabs(static_cast<double>(p.tr_f[row])) * exp(-static_cast<double>(p.tr_lq[row]));
+                    const double ww = (p.power == 2 ? rr * rr : rr) / p.wsum[pos];
+                    w[r] = isfinite(ww) ? static_cast<float>(ww) : 0.f;
+                }
+            }
+            // a point with a non-finite coordinate is skipped (all four lanes of its row agree)
+            int fin = isfinite(a[r][0]) && isfinite(a[r][1]);
+            fin &= __shfl_xor_sync(0xffffffffu, fin, 1);
+            fin &= __shfl_xor_sync(0xffffffffu, fin, 2);
+            if (!fin) {
+                a[r][0] = a[r][1] = 0.f;
+                w[r] = 0.f;
+            }
+            lq[r] = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (2 * t + h < d) lq[r] += softplusf(-a[r][h]) + softplusf(a[r][h]);   // -log x - log(1 - x)
+        }
+        // normalising pass
+#pragma unroll
+        for (int l = 0; l < FL_L; ++l) {
+            const bool inA0 = 2 * t < d && fl_in_A(l, 2 * t, d), inA1 = 2 * t + 1 < d && fl_in_A(l, 2 * t + 1, d);
+            const bool inB0 = 2 * t < d && !fl_in_A(l, 2 * t, d), inB1 = 2 * t + 1 < d && !fl_in_A(l, 2 * t + 1, d);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                al[l][r][0] = a[r][0];
+                al[l][r][1] = a[r][1];
+            }
+            float o[8];
+            fl_mlp_tile(s_fwd + l * FLP_LAYER_BYTES, inA0 ? a[0][0] : 0.f, inA1 ? a[0][1] : 0.f, inA0 ? a[1][0] : 0.f,
+                        inA1 ? a[1][1] : 0.f, o);
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (h ? inB1 : inB0) {
+                        const float s = FL_S * tanhf(o[r * 4 + h] / FL_S);
+                        a[r][h] = a[r][h] * __expf(s) + o[r * 4 + 2 + h];
+                        lq[r] += s;
+                    }
+        }
+        float gs[2][2];                      // dL/da of this lane's coordinates
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                gs[r][h] = 0.f;
+                if (2 * t + h < d) {
+                    lq[r] += -softplusf(-a[r][h]) - softplusf(a[r][h]);          // log z + log(1 - z)
+                    const float sg = 1.f / (1.f + __expf(-a[r][h]));
+                    gs[r][h] = -w[r] * (1.f - 2.f * sg);
+                }
+            }
+            float v = lq[r];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            if (t == 0 && valid[r]) {
+                loss += -static_cast<double>(w[r]) * v;
+                if (p.lq_out) p.lq_out[rbase + g + 8 * r] = v;
+            }
+        }
+        // reverse pass
+#pragma unroll
+        for (int l = FL_L - 1; l >= 0; --l) {
+            const unsigned char *lay = s_fwd + l * FLP_LAYER_BYTES;
+            const __nv_bfloat16 *W1n = s_bwd + l * FLB_HALVES + FLB_W1, *W2n = s_bwd + l * FLB_HALVES + FLB_W2,
+                                *W3n = s_bwd + l * FLB_HALVES + FLB_W3;
+            float *GL = s_g + l * FLG_LAYER;
+            const bool inA0 = 2 * t < d && fl_in_A(l, 2 * t, d), inA1 = 2 * t + 1 < d && fl_in_A(l, 2 * t + 1, d);
+            const bool inB0 = 2 * t < d && !fl_in_A(l, 2 * t, d), inB1 = 2 * t + 1 < d && !fl_in_A(l, 2 * t + 1, d);
+            const float i00 = inA0 ? al[l][0][0] : 0.f, i01 = inA1 ? al[l][0][1] : 0.f;
+            const float i10 = inA0 ? al[l][1][0] : 0.f, i11 = inA1 ? al[l][1][1] : 0.f;
+            uint32_t H1[4][4], H2[4][4];
+            float o[8];
+            fl_mlp_tile_keep(lay, i00, i01, i10, i11, H1, H2, o);
+            // dL/d(raw s) and dL/dt of this lane's coordinates (zero off B)
+            float ds[2][2], dt[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    ds[r][h] = 0.f;
+                    dt[r][h] = 0.f;
+                    if (h ? inB1 : inB0) {
+                        const float th = tanhf(o[r * 4 + h] / FL_S);
+                        const float es = __expf(FL_S * th);
+                        ds[r][h] = (gs[r][h] * al[l][r][h] * es - w[r]) * (1.f - th * th);
+                        dt[r][h] = gs[r][h];
+                        gs[r][h] *= es;
+                    }
+                }
+            // dout as the A fragment of K = 16 outputs (raw s columns 0..7, t columns 8..15)
+            const uint32_t dA0 = pack_bf16(ds[0][0], ds[0][1]), dA1 = pack_bf16(ds[1][0], ds[1][1]);
+            const uint32_t dA2 = pack_bf16(dt[0][0], dt[0][1]), dA3 = pack_bf16(dt[1][0], dt[1][1]);
+            // dout as B fragments with K = the 16 points: [output n-tile][points 0..7 / 8..15]
+            const uint32_t Bd[2][2] = {{mov_t(dA0), mov_t(dA1)}, {mov_t(dA2), mov_t(dA3)}};
+            // dW3 = H2^T dout (rows: hidden units), db3 = 1^T dout
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                const uint32_t a0 = mov_t(H2[mt][0]), a1 = mov_t(H2[mt][2]), a2 = mov_t(H2[mt][1]), a3 = mov_t(H2[mt][3]);
+#pragma unroll
+                for (int no = 0; no < 2; ++no) {
+                    float c[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_bf16(c, a0, a1, a2, a3, Bd[no][0], Bd[no][1]);
+                    float *G = GL + FLG_W3 + (16 * mt + g) * FLP_S1 + 8 * no + 2 * t;
+                    sadd_pair(G, c[0], c[1], swap);
+                    sadd_pair(G + 8 * FLP_S1, c[2], c[3], swap);
+                }
+            }
+#pragma unroll
+            for (int no = 0; no < 2; ++no) {
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_bf16(c, ONE2, ONE2, ONE2, ONE2, Bd[no][0], Bd[no][1]);
+                if (g == 0) {
+                    sadd(GL + FLG_B3 + 8 * no + 2 * t, c[0]);
+                    sadd(GL + FLG_B3 + 8 * no + 2 * t + 1, c[1]);
+                }
+            }
+            // dH2 = dout W3^T, masked by H2 > 0, as A fragments
+            uint32_t G2[4][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                const __nv_bfloat16 *col = W3n + (nt * 8 + g) * FLP_S1 + 2 * t;
+                mma_bf16(c, dA0, dA1, dA2, dA3, *reinterpret_cast<const uint32_t *>(col),
+                         *reinterpret_cast<const uint32_t *>(col + 8));
+                G2[nt >> 1][(nt & 1) * 2 + 0] = relu_mask_pack(c[0], c[1], H2[nt >> 1][(nt & 1) * 2 + 0]);
+                G2[nt >> 1][(nt & 1) * 2 + 1] = relu_mask_pack(c[2], c[3], H2[nt >> 1][(nt & 1) * 2 + 1]);
+            }
+            // dH1 = dH2 W2^T, masked by H1 > 0
+            uint32_t G1[4][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int kt = 0; kt < 4; ++kt) {
+                    const __nv_bfloat16 *col = W2n + (nt * 8 + g) * FLP_S2 + kt * 16 + 2 * t;
+                    mma_bf16(c, G2[kt][0], G2[kt][1], G2[kt][2], G2[kt][3], *reinterpret_cast<const uint32_t *>(col),
+                             *reinterpret_cast<const uint32_t *>(col + 8));
+                }
+                G1[nt >> 1][(nt & 1) * 2 + 0] = relu_mask_pack(c[0], c[1], H1[nt >> 1][(nt & 1) * 2 + 0]);
+                G1[nt >> 1][(nt & 1) * 2 + 1] = relu_mask_pack(c[2], c[3], H1[nt >> 1][(nt & 1) * 2 + 1]);
+            }
+            // dW2 = H1^T dH2, db2 = 1^T dH2
+            uint32_t H1T[4][4];
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                H1T[mt][0] = mov_t(H1[mt][0]);
+                H1T[mt][1] = mov_t(H1[mt][2]);
+                H1T[mt][2] = mov_t(H1[mt][1]);
+                H1T[mt][3] = mov_t(H1[mt][3]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const uint32_t b0 = mov_t(G2[nt >> 1][(nt & 1) * 2 + 0]), b1 = mov_t(G2[nt >> 1][(nt & 1) * 2 + 1]);
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) {
+                    float c[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_bf16(c, H1T[mt][0], H1T[mt][1], H1T[mt][2], H1T[mt][3], b0, b1);
+                    float *G = GL + FLG_W2 + (16 * mt + g) * FLP_S2 + 8 * nt + 2 * t;
+                    sadd_pair(G, c[0], c[1], swap);
+                    sadd_pair(G + 8 * FLP_S2, c[2], c[3], swap);
+                }
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_bf16(c, ONE2, ONE2, ONE2, ONE2, b0, b1);
+                if (g == 0) {
+                    sadd(GL + FLG_B2 + 8 * nt + 2 * t, c[0]);
+                    sadd(GL + FLG_B2 + 8 * nt + 2 * t + 1, c[1]);
+                }
+            }
+            // d(input) = dH1 W1^T (N = the 8 coordinates): reaches the conditioning coordinates
+            {
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int kt = 0; kt < 4; ++kt) {
+                    const __nv_bfloat16 *col = W1n + g * FLP_S2 + kt * 16 + 2 * t;
+                    mma_bf16(c, G1[kt][0], G1[kt][1], G1[kt][2], G1[kt][3], *reinterpret_cast<const uint32_t *>(col),
+                             *reinterpret_cast<const uint32_t *>(col + 8));
+                }
+                if (inA0) {
+                    gs[0][0] += c[0];
+                    gs[1][0] += c[2];
+                }
+                if (inA1) {
+                    gs[0][1] += c[1];
+                    gs[1][1] += c[3];
+                }
+            }
+            // dW1 = In^T dH1 with In's input column 8 set to one: row 8 of the product is db1
+            {
+                const uint32_t a0 = mov_t(pack_bf16(i00, i01)), a2 = mov_t(pack_bf16(i10, i11));
+                const uint32_t a1 = g == 0 ? ONE2 : 0u;
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const uint32_t b0 = mov_t(G1[nt >> 1][(nt & 1) * 2 + 0]), b1 = mov_t(G1[nt >> 1][(nt & 1) * 2 + 1]);
+                    float c[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_bf16(c, a0, a1, a2, a1, b0, b1);
+                    if (g < d) sadd_pair(GL + FLG_W1 + g * FLP_S2 + 8 * nt + 2 * t, c[0], c[1], swap);
+                    if (g == 0) {
+                        sadd(GL + FLG_B1 + 8 * nt + 2 * t, c[2]);
+                        sadd(GL + FLG_B1 + 8 * nt + 2 * t + 1, c[3]);
+                    }
+                }
+            }
+        }
+    }
+    // the block's gradient into the unit's (one atomic per nonzero entry), and its loss
+    __syncthreads();
+    float *G = p.grad + unit * FL_PARAMS;
+    for (int i = tid; i < FL_PARAMS; i += blockDim.x) {
+        const int l = i / FL_PER_LAYER, e = i % FL_PER_LAYER;
+        const float *GL = s_g + l * FLG_LAYER;
+        float v = 0.f;
+        if (e < FL_B1) {
+            const int k = (e - FL_W1) / FL_HID, n = (e - FL_W1) % FL_HID;
+            v = k < MAXD ? GL[FLG_W1 + k * FLP_S2 + n] : 0.f;         // inputs 8..15 are always zero
+        } else if (e < FL_W2) {
+            v = GL[FLG_B1 + e - FL_B1];
+        } else if (e < FL_B2) {
+            v = GL[FLG_W2 + (e - FL_W2) / FL_HID * FLP_S2 + (e - FL_W2) % FL_HID];
+        } else if (e < FL_W3) {
+            v = GL[FLG_B2 + e - FL_B2];
+        } else if (e < FL_B3) {
+            v = GL[FLG_W3 + (e - FL_W3) / FL_OUT * FLP_S1 + (e - FL_W3) % FL_OUT];
+        } else {
+            v = GL[FLG_B3 + e - FL_B3];
+        }
+        sadd(G + i, v);
+    }
+    loss += __shfl_xor_sync(0xffffffffu, loss, 16);
+    loss += __shfl_xor_sync(0xffffffffu, loss, 8);
+    loss += __shfl_xor_sync(0xffffffffu, loss, 4);
+    loss += __shfl_xor_sync(0xffffffffu, loss, 2);
+    loss += __shfl_xor_sync(0xffffffffu, loss, 1);
+    if (lane == 0) s_loss[warp] = loss;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int k = 0; k < nw; ++k) s += s_loss[k];
+        atomicAdd(p.loss + pos, s);
     }
 }
 
@@ -694,11 +849,9 @@ int flow_launch_sample(fiesta_ctx *c, FlowSampleParams &p, int64_t nu, int fp32,
     return FIESTA_OK;
 }
 
-constexpr size_t FLOW_TRAIN_SMEM = sizeof(float) * (FL_PARAMS + (FL_THREADS / 32) * 32 * 2 * FL_HID);
-
 int flow_launch_train(fiesta_ctx *c, FlowTrainParams &tp, int64_t nu) {
-    CUDA_TRY(cudaFuncSetAttribute(k_flow_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FLOW_TRAIN_SMEM));
-    k_flow_train<<<(unsigned)(nu * tp.blocks_per_unit), FL_THREADS, FLOW_TRAIN_SMEM, c->stream>>>(tp);
+    CUDA_TRY(cudaFuncSetAttribute(k_flow_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FLT_SMEM));
+    k_flow_train_tc<<<(unsigned)(nu * tp.blocks_per_unit), FLT_THREADS, FLT_SMEM, c->stream>>>(tp);
     CUDA_TRY(cudaGetLastError());
     return FIESTA_OK;
 }
@@ -862,7 +1015,9 @@ int fiesta_flow_train(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int32
     tp.loss = d_loss;
     tp.unit_begin = unit_begin;
     tp.keep = F->keep;
-    tp.blocks_per_unit = std::max<int64_t>(1, std::min<int64_t>((F->keep + 1023) / 1024, std::max<int64_t>(1, c->n_sm / nu)));
+    // about two blocks per SM over the slice (one resident at a time: 219 KB of shared
+    // memory), at least 256 training points per block
+    tp.blocks_per_unit = std::max<int64_t>(1, std::min<int64_t>((F->keep + 255) / 256, (2 * c->n_sm + nu - 1) / nu));
     tp.buf_unit0 = unit_begin;
     tp.power = power;
     const int64_t np = nu * FL_PARAMS;

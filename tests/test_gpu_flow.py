@@ -44,6 +44,64 @@ def _sampler_bf16(theta, z):
     return x, lq
 
 
+def _loss_grad_bf16(theta, x, w):
+    """L and dL/dtheta as the tensor-core training kernel computes them: the oracle's
+    reverse mode with BF16 rounding of every MMA operand (layer inputs, weights,
+    hidden activations, dout, dH2, dH1) and the ReLU masks taken on the rounded
+    activations; sums and the coupling arithmetic unrounded."""
+    n, d = x.shape
+    layers = F.unpack(theta)
+    M = F.masks(d)
+    a = np.log(x) - np.log1p(-x)
+    lq = -np.sum(np.log(x) + np.log1p(-x), axis=1)
+
+    def mlp(p, inp):
+        inb = _bf16(inp)
+        h1 = _bf16(np.maximum(inb @ _bf16(p["W1"]) + p["b1"], 0))
+        h2 = _bf16(np.maximum(h1 @ _bf16(p["W2"]) + p["b2"], 0))
+        return inb, h1, h2, h2 @ _bf16(p["W3"]) + p["b3"]
+
+    cache = []
+    for l in range(F.L_LAYERS):
+        B = ~M[l]
+        inp = F._cond_input(a, M[l])
+        inb, h1, h2, out = mlp(layers[l], inp)
+        s, t, raw = F._st(out, d)
+        cache.append((a.copy(), inb, h1, h2, raw))
+        a = np.where(B[None, :], a * np.exp(s) + t, a)
+        lq += np.sum(np.where(B[None, :], s, 0.0), axis=1)
+    sig = 1 / (1 + np.exp(-a))
+    lq += np.sum(-np.logaddexp(0, -a) - np.logaddexp(0, a), axis=1)
+    L = -np.sum(w * lq)
+    g = -w[:, None] * (1 - 2 * sig)
+    grad = np.zeros_like(theta)
+    gl = F.unpack(grad)
+    for l in reversed(range(F.L_LAYERS)):
+        A, B = M[l], ~M[l]
+        a_in, inb, h1, h2, raw = cache[l]
+        p, gp = layers[l], gl[l]
+        th = np.tanh(raw / F.S_BOUND)
+        es = np.exp(F.S_BOUND * th)
+        ds = np.where(B[None, :], (g * a_in * es - w[:, None]) * (1 - th * th), 0.0)
+        dt = np.where(B[None, :], g, 0.0)
+        g_in = np.where(B[None, :], g * es, g)
+        dout = np.zeros((n, F.OUT))
+        dout[:, :d] = ds
+        dout[:, 8:8 + d] = dt
+        dout = _bf16(dout)
+        gp["W3"] += h2.T @ dout
+        gp["b3"] += dout.sum(0)
+        dh2 = _bf16((dout @ _bf16(p["W3"]).T) * (h2 > 0))
+        gp["W2"] += h1.T @ dh2
+        gp["b2"] += dh2.sum(0)
+        dh1 = _bf16((dh2 @ _bf16(p["W2"]).T) * (h1 > 0))
+        gp["W1"] += inb.T @ dh1
+        gp["b1"] += dh1.sum(0)
+        dinp = dh1 @ _bf16(p["W1"]).T
+        g = g_in + np.where(A[None, :], dinp[:, :d], 0.0)
+    return L, lq, grad
+
+
 def _random_theta(seed):
     rng = np.random.default_rng(seed)
     th = F.init_params(rng, 0.15)
@@ -77,14 +135,23 @@ def test_flow_kernels_match_oracle(dim):
     # integrand at the sampled points
     fx = 0.25 + sum((j + 1.5) * out["x"][:, j] for j in range(dim))
     assert np.max(np.abs(out["f"] - fx) / fx) < 1e-12
-    # training pass (binary32) against the oracle in binary64, at the sampler's x
+    # training pass (tensor cores, BF16 operands, binary32 accumulation) at the sampler's
+    # x: against its rounding emulation closely, and against the oracle's binary64
+    # reverse mode within what BF16 operands allow
     X = out["x"]
-    lq64 = F.log_q(th, X)
-    assert np.max(np.abs(out["logq_train"] - lq64)) < 2e-3
+    Le, lqe, ge = _loss_grad_bf16(th, X, w)
+    dl = np.abs(out["logq_train"] - lqe)
+    assert np.median(dl) < 1e-4 and np.max(dl) < 2e-2, (np.median(dl), np.max(dl))
+    assert abs(out["loss"] - Le) <= 1e-3 * max(1.0, abs(Le))
+    gmax = np.max(np.abs(ge))
+    de = np.abs(out["grad"] - ge) / gmax
+    print(f"grad vs emulation: median {np.median(de):.2e}, max {np.max(de):.2e}")
+    assert np.max(de) <= 2e-3 and np.median(de) <= 1e-6, (np.median(de), np.max(de))
     L, g = F.loss_and_grad(th, X, w)
-    assert abs(out["loss"] - L) <= 1e-3 * max(1.0, abs(L))
-    gmax = np.max(np.abs(g))
-    assert np.max(np.abs(out["grad"] - g)) <= 2e-3 * gmax, np.max(np.abs(out["grad"] - g)) / gmax
+    assert abs(out["loss"] - L) <= 1e-2 * max(1.0, abs(L))
+    d64 = np.abs(out["grad"] - g) / np.max(np.abs(g))
+    print(f"grad vs binary64 oracle: median {np.median(d64):.2e}, max {np.max(d64):.2e}")
+    assert np.max(d64) <= 3e-2, np.max(d64)
 
 
 def test_flow_estimates_are_unbiased_on_the_box():
