@@ -185,6 +185,20 @@ def test_deterministic_without_adaptation():
     assert [u["value"] for u in a.per_unit] == [u["value"] for u in b.per_unit]
 
 
+def test_adapted_runs_reproduce_to_rounding():
+    """Adapted runs repeat up to the summation order of the grid histogram: each block
+    sums its points' v^2 into shared-memory bins with binary64 atomics and adds them to
+    the unit's histogram in the order the blocks finish, so grid edges can differ in
+    their last bits between runs; the repeated run's per-unit values agree far below
+    their statistical errors."""
+    need_gpu()
+    integ = integrator("box")
+    a = integ.integrate(n_iter=5, points=50_000, seed=21)
+    b = integ.integrate(n_iter=5, points=50_000, seed=21)
+    for ua, ub in zip(a.per_unit, b.per_unit):
+        assert abs(ua["value"] - ub["value"]) <= 1e-10 * abs(ua["value"]) + 1e-6 * ua["sigma"], (ua, ub)
+
+
 def test_timeout_returns_cleanly():
     need_gpu()
     from paper_1511_03614_gb300._native import FiestaError
