@@ -183,7 +183,8 @@ def op_costs(peaks):
     log_c = fma_rate / (peaks[6] * 1e9)
     div_c = fma_rate / (peaks[2] * 1e9)
     atan_c = fma_rate / (peaks[7] * 1e9) if len(peaks) > 7 and peaks[7] > 0 else log_c
-    return {"LOG": log_c, "DIV": div_c, "INV": div_c, "ATAN2": atan_c}
+    inv_c = fma_rate / (peaks[8] * 1e9) if len(peaks) > 8 and peaks[8] > 0 else div_c
+    return {"LOG": log_c, "DIV": div_c, "INV": inv_c, "ATAN2": atan_c}
 
 
 def unit_work(prog, costs, dim, n_out):
@@ -278,7 +279,8 @@ def roofline_of(prep, res, peaks, pts, pass_s, args, iters):
             "eval_launches_per_pass": res.stats["eval_launches"] // max(iters, 1) if res else None,
             "peaks_measured": {"fp64_tflops": peaks[0], "fp64_log_cuda_gps": peaks[1], "fp64_div_gps": peaks[2],
                                "fp32_tflops": peaks[3], "fp32_log_gps": peaks[4], "fp32_div_gps": peaks[5],
-                               "fp64_log_table_gps": peaks[6], "fp64_atan2_gps": peaks[7]},
+                               "fp64_log_table_gps": peaks[6], "fp64_atan2_gps": peaks[7],
+                               "fp64_recip_gps": peaks[8]},
             "op_costs_fma_slots": {"fp64": costs, "fp32": costs32}}
 
 
@@ -295,8 +297,8 @@ def run_ours(args):
     iters = args.iters or iters
     prep = prepared(args.workload, args.fuse)
     lib = N.load()
-    peaks = (C.c_double * 8)()
-    N.check(lib.fiesta_probe_peaks(peaks, 8))
+    peaks = (C.c_double * 9)()
+    N.check(lib.fiesta_probe_peaks(peaks, 9))
     peaks = list(peaks)
     integ = Integrator(prep)
     # replicas: every rank integrates every unit with its own point streams (weak scaling)

@@ -456,8 +456,9 @@ int fiesta_cuhre_regions(fiesta_ctx *ctx, int64_t unit, int64_t cap, double *cen
  * instruction mix into a lower bound on its evaluation time.  out (host, >= 7
  * doubles): [0] binary64 FMA TFLOP/s, [1] binary64 log (CUDA's) G/s, [2]
  * binary64 divide G/s, [3] binary32 FMA TFLOP/s, [4] binary32 logf G/s, [5]
- * binary32 divide G/s, [6] the interpreter's table-driven binary64 log G/s, and
- * when n >= 8, [7] binary64 atan2 G/s.
+ * binary32 divide G/s, [6] the interpreter's table-driven binary64 log G/s,
+ * when n >= 8, [7] binary64 atan2 G/s, and when n >= 9, [8] the interpreter's
+ * binary64 reciprocal (Newton-Raphson refinement) G/s.
  * Allocates and frees small scratch buffers.
  */
 int fiesta_probe_peaks(double *out, int32_t n);

@@ -133,7 +133,7 @@ __device__ __noinline__ void exec_special(uint32_t op, uint32_t a, uint32_t b, u
     case 6: r = va / E[b + (b >= pt ? tid : 0)]; break;
     case 12: r = dev_powi<T>(va, static_cast<int>(static_cast<int8_t>(b & 0xffu))); break;
     case 13: r = interp_log<T>(va, logtab); break;
-    case 14: r = T(1) / va; break;
+    case 14: r = dev_recip<T>(va); break;
     case 16: r = dev_atan2<T>(va, E[b + (b >= pt ? tid : 0)]); break;
     default: r = T(0); break;
     }

@@ -241,6 +241,36 @@ def test_table_log_within_one_ulp():
         assert max(ulps) <= 1.0, max(ulps)
 
 
+def test_reciprocal_within_one_ulp():
+    """The interpreter's binary64 reciprocal (Newton-Raphson refinement of the hardware's
+    approximate reciprocal) against the exact value: within 1 ulp over the whole
+    exponent range, both signs, and IEEE results for zero, subnormal and overflowing
+    arguments (the cases that take the IEEE division)."""
+    need_gpu()
+    from paper_1511_03614_gb300 import parse_text, Integrator
+    rng = np.random.default_rng(17)
+    x = np.concatenate([np.exp(rng.uniform(-740, 0, 6000)), rng.uniform(0.5, 1, 2000),
+                        [2.0 ** -1022, 2.0 ** -1021, 2.0 ** -1020, 1.0, 0.75, 1 - 2.0 ** -53]])
+    for text, scale in (("1; 0; p[x[1],-1]; |", 1.0), ("1; 0; p[x[1]*1e300,-1]; |", 1e300),
+                        ("1; 0; p[x[1]*-3.0,-1]; |", -3.0), ("1; 0; p[x[1]*1.7976931348623157e308,-1]; |",
+                                                            1.7976931348623157e308)):
+        integ = Integrator(parse_text(text))
+        got = integ.eval_batch(0, x[:, None])
+        arg = x * scale
+        with np.errstate(divide="ignore", over="ignore"):
+            ieee = 1.0 / arg
+        special = ~np.isfinite(ieee) | (np.abs(arg) < 2.0 ** -1021) | (np.abs(arg) >= 2.0 ** 1022)
+        assert np.array_equal(got[special], ieee[special])
+        with mp.workdps(40):
+            ulps = [float(abs(mp.mpf(float(g)) - 1 / mp.mpf(float(a))) / math.ulp(float(r)))
+                    for g, a, r in zip(got[~special], arg[~special], ieee[~special])]
+        assert max(ulps) <= 1.0, max(ulps)
+    integ = Integrator(parse_text("1; 0; p[x[1],-1]; |"))
+    z = np.array([[0.0], [5e-324], [2.0 ** -1030]])
+    with np.errstate(divide="ignore"):
+        assert np.array_equal(integ.eval_batch(0, z), 1.0 / z[:, 0])
+
+
 def test_precision_probe_and_auto_mode():
     """The per-unit binary32 probe and FIESTA_AUTO: box results stay within errors of the closed form."""
     need_gpu()
