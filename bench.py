@@ -227,7 +227,7 @@ def op_costs32(peaks):
 # memory, so this does not grow with the number of points.  None: not captured for
 # the current kernel.
 TRAFFIC = {("double_box", "fp64", True): (
-    41250560 + 40871936 + 1612544,
+    41406976 + 41015552 + 1403392,
     "ncu dram__bytes_read.sum + dram__bytes_write.sum of the two k_eval<double, Philox, 6, registers> launches of "
     "one evaluation pass at the bench's size and shapes (bench.py --mode kernel --workload double_box --points "
     "10000000 --threads 384 --ppt 8 --wide-threads 384): mostly the (unit, chunk) partial sums of the fixed-order "
