@@ -135,7 +135,7 @@ __device__ __forceinline__ void fl_mlp_tile(const unsigned char *__restrict__ la
 
 struct FlowSampleParams {
     const DevUnit *units;
-    const uint32_t *code;
+    const uint64_t *pre;               // forwarded programs (uops.cuh)
     const double *cons64;
     const float *cons32;
     const double *logtab;
@@ -163,24 +163,42 @@ __global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) 
     const int64_t blk = blockIdx.x % p.blocks_per_unit;
     const DevUnit u = p.units[unit];
     const int d = u.dim;
+    // the program runs in its micro-op form (uops.cuh): shared memory viewed as T holds
+    // the constants (then -0, 1, -1) below pt, and from pt on this block's coordinates
+    // and slot file, [index][thread]
     size_t off = 0;
     unsigned char *s_flow = smem; off = align16(off + FLP_UNIT_BYTES);
-    uint32_t *s_code = reinterpret_cast<uint32_t *>(smem + off); off = align16(off + 4 * p.max_instr);
-    T *s_cons = reinterpret_cast<T *>(smem + off); off = align16(off + sizeof(T) * p.max_const);
+    uint64_t *s_uops = reinterpret_cast<uint64_t *>(smem + off); off = align16(off + 8 * (p.max_instr + 1));
+    T *s_cons = reinterpret_cast<T *>(smem + off); off = align16(off + sizeof(T) * (p.max_const + 3));
     double *s_tab = reinterpret_cast<double *>(smem + off); off = align16(off + 8 * LOGTAB_DOUBLES);
     T *s_x = reinterpret_cast<T *>(smem + off); off = align16(off + sizeof(T) * MAXD * nt);
     T *s_slots = reinterpret_cast<T *>(smem + off); off = align16(off + sizeof(T) * p.max_slots * nt);
     float *s_lq = reinterpret_cast<float *>(smem + off); off = align16(off + 4 * nt);
-    float *s_xf = reinterpret_cast<float *>(smem + off); off = align16(off + 4 * MAXD * nt);
-    float *s_af = reinterpret_cast<float *>(smem + off); off = align16(off + 4 * MAXD * nt);
+    // x and logit(x) in binary32, rows of nt + 4: the four lanes t of a row group g that
+    // write one coordinate land in distinct banks
+    const int xs = nt + 4;
+    float *s_xf = reinterpret_cast<float *>(smem + off); off = align16(off + 4 * MAXD * xs);
+    float *s_af = reinterpret_cast<float *>(smem + off); off = align16(off + 4 * MAXD * xs);
     double *s_acc = reinterpret_cast<double *>(smem + off); off = align16(off + 8 * 2 * MAXO * nt);
     double *s_red = reinterpret_cast<double *>(smem + off);
+    T *E = reinterpret_cast<T *>(smem);
+    const int cons_base = static_cast<int>((reinterpret_cast<unsigned char *>(s_cons) - smem) / sizeof(T));
+    const int k_zero = cons_base + p.max_const;
+    const int pt = static_cast<int>((reinterpret_cast<unsigned char *>(s_x) - smem) / sizeof(T));
+    const int slot_base = static_cast<int>((reinterpret_cast<unsigned char *>(s_slots) - smem) / sizeof(T));
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(p.packed + unit * FLP_UNIT_BYTES);
         uint4 *dst = reinterpret_cast<uint4 *>(s_flow);
         for (int i = tid; i < (int)(FLP_UNIT_BYTES / 16); i += nt) dst[i] = src[i];
     }
-    for (int i = tid; i < u.n_instr; i += nt) s_code[i] = p.code[u.code_off + i];
+    for (int i = tid; i < u.n_uop; i += nt)
+        s_uops[i] = uop_from_pre(p.pre[u.uop_off + i], cons_base, k_zero, pt, slot_base, nt);
+    if (tid == 0) {
+        s_uops[u.n_uop] = 0ull;                          // fetched after the last word, never executed
+        s_cons[p.max_const] = T(-0.0);
+        s_cons[p.max_const + 1] = T(1);
+        s_cons[p.max_const + 2] = T(-1);
+    }
     for (int i = tid; i < u.n_const; i += nt)
         s_cons[i] = sizeof(T) == 8 ? static_cast<T>(p.cons64[u.const_off + i]) : static_cast<T>(p.cons32[u.const_off + i]);
     for (int i = tid; i < LOGTAB_DOUBLES; i += nt) s_tab[i] = p.logtab[i];
@@ -256,8 +274,8 @@ __global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) 
                 const float av = a[r][h];
                 lq[r] += softplusf(-av) + softplusf(av);
                 const float xv = 1.f / (1.f + __expf(-av));
-                s_xf[(2 * t + h) * nt + warp * 32 + row] = xv;
-                s_af[(2 * t + h) * nt + warp * 32 + row] = av;
+                s_xf[(2 * t + h) * xs + warp * 32 + row] = xv;
+                s_af[(2 * t + h) * xs + warp * 32 + row] = av;
             }
             float v = lq[r];
             v += __shfl_xor_sync(0xffffffffu, v, 1);
@@ -268,12 +286,12 @@ __global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) 
         // every lane evaluates its own point
         const int64_t pi = wbase + lane;
         const float lqv = s_lq[tid];
-        for (int j = 0; j < d; ++j) s_x[j * nt + tid] = static_cast<T>(s_xf[j * nt + tid]);
-        (void)interpret<T>(s_code, u.n_instr, s_cons, s_slots + tid, s_x + tid, nt, u.out_slot, s_tab);
+        for (int j = 0; j < d; ++j) s_x[j * nt + tid] = static_cast<T>(s_xf[j * xs + tid]);
+        interpret_uop<T>(s_uops, u.n_uop, E, pt, tid, s_tab);
         // a coordinate below the binary32 range (x = sigmoid(a) underflows; measure
         // < 1e-38 per coordinate) makes the point contribute zero
         bool in_range = true;
-        for (int j = 0; j < d; ++j) in_range = in_range && s_xf[j * nt + tid] >= 1.17549435e-38f;
+        for (int j = 0; j < d; ++j) in_range = in_range && s_xf[j * xs + tid] >= 1.17549435e-38f;
         if (pi < last) {
             const double iq = exp(-static_cast<double>(lqv));
             bool finite = true;
@@ -294,14 +312,14 @@ __global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) 
                 // training points are kept as logit coordinates a (x may round to 1 in binary32);
                 // the target of a unit with several results is the norm of its result vector
                 float *dst = p.tr_x + (unit * p.keep + pi) * MAXD;
-                for (int j = 0; j < MAXD; ++j) dst[j] = j < d ? s_af[j * nt + tid] : 0.f;
+                for (int j = 0; j < MAXD; ++j) dst[j] = j < d ? s_af[j * xs + tid] : 0.f;
                 p.tr_lq[unit * p.keep + pi] = lqv;
                 p.tr_f[unit * p.keep + pi] = static_cast<float>(no == 1 ? f0 : sqrt(f2));
             }
             if (p.x_out) {
                 for (int j = 0; j < d; ++j) {
-                    p.x_out[pi * d + j] = s_xf[j * nt + tid];
-                    p.a_out[pi * d + j] = s_af[j * nt + tid];
+                    p.x_out[pi * d + j] = s_xf[j * xs + tid];
+                    p.a_out[pi * d + j] = s_af[j * xs + tid];
                 }
                 p.lq_out[pi] = lqv;
                 p.f_out[pi] = f0;
@@ -826,9 +844,9 @@ int flow_alloc(fiesta_ctx *c, int64_t keep) {
 
 size_t flow_sample_smem(int fp32, const SliceInfo &si) {
     const size_t T = fp32 ? 4 : 8;
-    return align16(FLP_UNIT_BYTES) + align16(4 * si.max_instr) + align16(T * si.max_const) +
+    return align16(FLP_UNIT_BYTES) + align16(8 * (si.max_instr + 1)) + align16(T * (si.max_const + 3)) +
            align16(8 * LOGTAB_DOUBLES) + align16(T * MAXD * FL_THREADS) + align16(T * si.max_slots * FL_THREADS) +
-           align16(4 * FL_THREADS) + 2 * align16(4 * MAXD * FL_THREADS) + align16(8 * 2 * MAXO * FL_THREADS) +
+           align16(4 * FL_THREADS) + 2 * align16(4 * MAXD * (FL_THREADS + 4)) + align16(8 * 2 * MAXO * FL_THREADS) +
            (2 * MAXO * 8 + 8) * 32 + 64;
 }
 
@@ -915,7 +933,7 @@ int fiesta_flow_sample(fiesta_ctx *c, int64_t unit_begin, int64_t unit_end, int6
     if (r) return r;
     FlowSampleParams p{};
     p.units = c->d_units;
-    p.code = c->d_code;
+    p.pre = c->d_pre;
     p.cons64 = c->d_cons64;
     p.cons32 = c->d_cons32;
     p.logtab = c->d_logtab;
@@ -1092,7 +1110,7 @@ int fiesta_flow_check(fiesta_ctx *c, int64_t unit, int64_t n, int32_t precision,
         FlowSampleParams p{};
         p.out_stride = c->units[unit].n_out;
         p.units = c->d_units;
-        p.code = c->d_code;
+        p.pre = c->d_pre;
         p.cons64 = c->d_cons64;
         p.cons32 = c->d_cons32;
         p.logtab = c->d_logtab;
