@@ -39,7 +39,8 @@ constexpr int FLP_BIAS = FL_HID + FL_HID + FL_OUT;                   // 144 floa
 constexpr size_t FLP_LAYER_BYTES = FLP_HALVES * 2 + FLP_BIAS * 4;    // 15168
 constexpr size_t FLP_UNIT_BYTES = FLP_LAYER_BYTES * FL_L;            // 60672
 constexpr float FL_S = 4.0f;
-constexpr int FL_THREADS = 128;
+constexpr int FL_THREADS = 128;                  // sampler block; FL_THREADS_MAX when only one block fits an SM
+constexpr int FL_THREADS_MAX = 256;
 
 __device__ __forceinline__ bool fl_in_A(int l, int j, int d) {
     const int half = (d + 1) >> 1;
@@ -155,7 +156,7 @@ struct FlowSampleParams {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(FL_THREADS) k_flow_sample(FlowSampleParams p) {
+__global__ void __launch_bounds__(FL_THREADS_MAX) k_flow_sample(FlowSampleParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -842,26 +843,34 @@ int flow_alloc(fiesta_ctx *c, int64_t keep) {
     return FIESTA_OK;
 }
 
-size_t flow_sample_smem(int fp32, const SliceInfo &si) {
+size_t flow_sample_smem(int fp32, const SliceInfo &si, int nt) {
     const size_t T = fp32 ? 4 : 8;
     return align16(FLP_UNIT_BYTES) + align16(8 * (si.max_instr + 1)) + align16(T * (si.max_const + 3)) +
-           align16(8 * LOGTAB_DOUBLES) + align16(T * MAXD * FL_THREADS) + align16(T * si.max_slots * FL_THREADS) +
-           align16(4 * FL_THREADS) + 2 * align16(4 * MAXD * (FL_THREADS + 4)) + align16(8 * 2 * MAXO * FL_THREADS) +
+           align16(8 * LOGTAB_DOUBLES) + align16(T * MAXD * nt) + align16(T * si.max_slots * nt) +
+           align16(4 * nt) + 2 * align16(4 * MAXD * (nt + 4)) + align16(8 * 2 * MAXO * nt) +
            (2 * MAXO * 8 + 8) * 32 + 64;
 }
 
 int flow_launch_sample(fiesta_ctx *c, FlowSampleParams &p, int64_t nu, int fp32, const SliceInfo &si) {
-    const size_t sm = flow_sample_smem(fp32, si);
-    int dev_max = 0;
+    int dev_max = 0, sm_max = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&sm_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
+    // 128-thread blocks (two per SM by registers); when the flow, the program and the
+    // slot files leave room for only one such block, 256 threads share one staged flow
+    int nt = FL_THREADS;
+    size_t sm = flow_sample_smem(fp32, si, nt);
+    if (2 * (sm + 1024) > (size_t)sm_max && flow_sample_smem(fp32, si, FL_THREADS_MAX) <= (size_t)dev_max) {
+        nt = FL_THREADS_MAX;
+        sm = flow_sample_smem(fp32, si, nt);
+    }
     if ((int)sm > dev_max) return fail(FIESTA_E_NOMEM, "flow sampler: program too large for shared memory");
     const unsigned blocks = (unsigned)(nu * p.blocks_per_unit);
     if (fp32) {
         CUDA_TRY(cudaFuncSetAttribute(k_flow_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_flow_sample<float><<<blocks, FL_THREADS, sm, c->stream>>>(p);
+        k_flow_sample<float><<<blocks, nt, sm, c->stream>>>(p);
     } else {
         CUDA_TRY(cudaFuncSetAttribute(k_flow_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_flow_sample<double><<<blocks, FL_THREADS, sm, c->stream>>>(p);
+        k_flow_sample<double><<<blocks, nt, sm, c->stream>>>(p);
     }
     CUDA_TRY(cudaGetLastError());
     return FIESTA_OK;
