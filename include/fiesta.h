@@ -303,6 +303,14 @@ typedef struct {
     double ratio;              /* max over orders of |error| / target after the last check */
     int64_t points_per_replicate; /* RQMC: the last Sobol length */
     double rel_tol;            /* CUHRE: the last per-unit tolerance */
+    double *order_sw, *order_swi; /* RQMC, nullable (caller-owned, 2 * n_out_orders entries each: the
+                                 real parts, then the imaginary parts): per assembled order,
+                                 running sums of 1/var and mean/var of the assembled series
+                                 formed replicate by replicate.  When set, rounds are combined
+                                 per assembled order, so the correlation of a fused unit's orders
+                                 (evaluated at the same points) enters the error as measured
+                                 instead of through opt->correlated's bound; the per-result
+                                 sums sw, swi are kept as well. */
 } fiesta_accuracy_state;
 
 int fiesta_integrate_to_accuracy(fiesta_ctx *ctx, const fiesta_accuracy_options *opt, fiesta_accuracy_state *state,

@@ -63,7 +63,8 @@ class AccuracyOptions(C.Structure):
 class AccuracyState(C.Structure):
     _fields_ = [("sw", C.POINTER(C.c_double)), ("swi", C.POINTER(C.c_double)), ("n_used", C.POINTER(C.c_double)),
                 ("iterations", C.c_int32), ("converged", C.c_int32), ("gpu_ms", C.c_double), ("points", C.c_int64),
-                ("ratio", C.c_double), ("points_per_replicate", C.c_int64), ("rel_tol", C.c_double)]
+                ("ratio", C.c_double), ("points_per_replicate", C.c_int64), ("rel_tol", C.c_double),
+                ("order_sw", C.POINTER(C.c_double)), ("order_swi", C.POINTER(C.c_double))]
 
 
 class UnitResult(C.Structure):

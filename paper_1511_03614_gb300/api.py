@@ -460,7 +460,9 @@ def accuracy_options(prep, method="vegas", proposal="vegas", target=1e-4, floor=
 def new_accuracy_state(prep):
     """Zeroed running sums for fiesta_integrate_to_accuracy (numpy arrays + the struct)."""
     nrec = sum(u.n_out for u in prep.units)
-    arrays = dict(sw=np.zeros(nrec), swi=np.zeros(nrec), n_used=np.zeros(len(prep.units)))
+    n_orders = len(prep.out_orders)
+    arrays = dict(sw=np.zeros(nrec), swi=np.zeros(nrec), n_used=np.zeros(len(prep.units)),
+                  order_sw=np.zeros(2 * n_orders), order_swi=np.zeros(2 * n_orders))
     st = N.AccuracyState()
     for k, v in arrays.items():
         setattr(st, k, v.ctypes.data_as(C.POINTER(C.c_double)))

@@ -326,9 +326,19 @@ extern "C" int fiesta_integrate_to_accuracy(fiesta_ctx *c, const fiesta_accuracy
     const size_t nrec = recs.size();
     std::vector<double> val, sig;
     const auto capped = [&]() { return o->max_gpu_s > 0.0 && st->gpu_ms * 1e-3 >= o->max_gpu_s; };
+    // RQMC with per-order sums: the assembled values and errors come from them
+    const bool per_order = o->method == FIESTA_METHOD_RQMC && st->order_sw && st->order_swi;
     const auto check = [&](bool linear) {
         estimates(st, nrec, val, sig);
-        const Series S = assemble_series(recs, val.data(), sig.data(), o, n_out, linear);
+        Series S = assemble_series(recs, val.data(), sig.data(), o, n_out, linear);
+        if (per_order)
+            for (int n = 0; n < n_out; ++n) {
+                const double w = st->order_sw[n], wi = st->order_sw[n_out + n];
+                S.re[n] = w > 0.0 ? st->order_swi[n] / w : 0.0;
+                S.ere[n] = w > 0.0 ? std::sqrt(1.0 / w) : HUGE_VAL;
+                S.im[n] = wi > 0.0 ? st->order_swi[n_out + n] / wi : 0.0;
+                S.eim[n] = wi > 0.0 ? std::sqrt(1.0 / wi) : 0.0;
+            }
         st->ratio = worst_ratio(S, o->target, o->floor);
         st->converged = st->ratio <= 1.0 ? 1 : 0;
         write_outputs(S, recs, st, n_out, value, error, value_im, error_im, unit_value, unit_sigma);
@@ -474,6 +484,41 @@ extern "C" int fiesta_integrate_to_accuracy(fiesta_ctx *c, const fiesta_accuracy
                 const double w = var > 0.0 ? 1.0 / var : 1e300;
                 st->sw[k] += w;
                 st->swi[k] += w * mu;
+            }
+            if (per_order) {
+                // the assembled series of every replicate (its records' replicate means
+                // through the prefactor), then per order the replicate mean and spread
+                std::vector<double> mj(nrec), zero(nrec, 0.0);
+                std::vector<double> a_re((size_t)R * n_out), a_im((size_t)R * n_out);
+                for (int j = 0; j < R; ++j) {
+                    for (size_t k = 0; k < nrec; ++k) {
+                        double m, v;
+                        iteration_of(c, recs[k], j, m, v);
+                        mj[k] = m;
+                    }
+                    const Series A = assemble_series(recs, mj.data(), zero.data(), o, n_out, false);
+                    for (int n = 0; n < n_out; ++n) {
+                        a_re[(size_t)j * n_out + n] = A.re[n];
+                        a_im[(size_t)j * n_out + n] = A.im[n];
+                    }
+                }
+                for (int p = 0; p < 2; ++p) {
+                    const std::vector<double> &a = p ? a_im : a_re;
+                    for (int n = 0; n < n_out; ++n) {
+                        double mu = 0.0, ss = 0.0;
+                        for (int j = 0; j < R; ++j) mu += a[(size_t)j * n_out + n];
+                        mu /= R;
+                        for (int j = 0; j < R; ++j) {
+                            const double d = a[(size_t)j * n_out + n] - mu;
+                            ss += d * d;
+                        }
+                        const double var = ss / (R - 1) / R;
+                        if (p && var == 0.0 && mu == 0.0) continue;       // no imaginary part
+                        const double w = var > 0.0 ? 1.0 / var : 1e300;
+                        st->order_sw[p * n_out + n] += w;
+                        st->order_swi[p * n_out + n] += w * mu;
+                    }
+                }
             }
             st->points_per_replicate = n;
             st->iterations = rnd + 1;

@@ -127,6 +127,44 @@ def test_rqmc_loop_uses_the_replicate_spread():
     assert state[0].points_per_replicate == 1 << 12
 
 
+@pytest.mark.parametrize("name", ["box", "box_physical"])
+def test_rqmc_assembles_each_replicate(name):
+    """One round of FIESTA_METHOD_RQMC on fused units: each assembled order's value is
+    the mean over the replicates of the series assembled from that replicate's results
+    (through the prefactor), and its error their spread over sqrt(replicates), so the
+    correlation between a fused unit's orders enters as measured."""
+    need_gpu()
+    from paper_1511_03614_gb300 import prepare_feynman, Integrator
+    from paper_1511_03614_gb300.api import integrate_to_accuracy, _records
+    import workloads as W
+    prep = prepare_feynman(getattr(W, name)(), fuse_orders=True)
+    integ = Integrator(prep)
+    recs = _records(prep)
+    R = 8
+    res, _ = integrate_to_accuracy(integ, method="rqmc", target=1e-12, points=1 << 12, replicates=R,
+                                   adapt_iters=2, max_iters=1, seed=7)
+    q, c = prep.prefactor
+    orders = list(prep.out_orders)
+    A = np.zeros((R, len(orders)), dtype=complex)
+    for j in range(R):
+        I = {}
+        for (u, o) in recs:
+            unit = prep.units[u]
+            m, _ = integ.iterations(u, R, o)
+            K = unit.order + (o // 2 if unit.cplx else o)
+            I[K] = I.get(K, 0) + (1j * m[j] if unit.cplx and o % 2 else m[j])
+        for a, n in enumerate(orders):
+            A[j, a] = sum(ci * I.get(n - (i - q), 0) for i, ci in enumerate(c))
+    for a, n in enumerate(orders):
+        mean, err = res["values"][n], res["errors"][n]
+        for part in (np.real, np.imag):
+            x = part(A[:, a])
+            if np.all(x == 0):
+                continue
+            assert math.isclose(part(mean), np.mean(x), rel_tol=1e-11, abs_tol=1e-13), (n, part(mean), np.mean(x))
+            assert math.isclose(part(err), math.sqrt(np.var(x, ddof=1) / R), rel_tol=1e-8), (n, part(err))
+
+
 def test_flow_proposal_in_fiesta_integrate():
     """fiesta_options.proposal = FLOW: iterations drawn from the units' flows, trained
     between iterations; the box's closed form within 4 sigma of the combined result."""
