@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=256, help="kernel mode: threads per block")
     ap.add_argument("--ppt", type=int, default=8, help="kernel mode: points per thread per work item")
     ap.add_argument("--units", type=int, default=0, help="kernel mode, stress: the first N integrands (0: all)")
+    ap.add_argument("--stress-orders", default="one", choices=["one", "all"],
+                    help="stress: one eps coefficient per integrand (10 000 units) or every one of eps^0..eps^2")
     ap.add_argument("--launch-shape", default="",
                     help="throughput mode: threads,points_per_thread,wide_threads instead of the autotuner's")
     ap.add_argument("--wide-threads", type=int, default=0,
@@ -80,11 +82,14 @@ def parse():
     return ap.parse_args()
 
 
+STRESS_ALL_ORDERS = False      # --stress-orders all: every integrand's eps^0..eps^2 coefficients
+
+
 def prepared(workload, fuse=False, mix=1, terms=False):
     import workloads as W
     from paper_1511_03614_gb300 import prepare_feynman, prepare_direct
     if workload == "stress":
-        return prepare_direct(W.stress_suite(), "stress")
+        return prepare_direct(W.stress_suite(all_orders=STRESS_ALL_ORDERS), "stress")
     return prepare_feynman(getattr(W, workload)(), fuse_orders=bool(fuse), mix_sectors=mix,
                            separate_terms=bool(terms))
 
@@ -399,7 +404,10 @@ def run_ours(args):
                                                   "293 sectors x 6 dims (1141 sector-order integrands), Vegas 1 it "
                                                   "x 1e7 Philox points per sector per step, grid refined after it "
                                                   "(20 steps: 2e8 points per sector)",
-                                    "stress": "10000 seeded synthetic integrands, dims 3..8, 2^20 Sobol points"
+                                    "stress": ("10000 seeded synthetic integrands, dims 3..8, "
+                                               + ("each expanded to eps^0..eps^2 (one unit per coefficient), "
+                                                  if STRESS_ALL_ORDERS else "one eps coefficient each, ")
+                                               + "2^20 Sobol points per unit")
                                     }[args.workload],
                        "units": len(prep.units), "points_per_unit_per_iter": pts, "iterations": iters,
                        "fused_orders": bool(args.fuse) and args.workload != "stress",
@@ -813,7 +821,9 @@ def run_flow_kernels(args):
 
 
 def main():
+    global STRESS_ALL_ORDERS
     args = parse()
+    STRESS_ALL_ORDERS = args.stress_orders == "all"
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "kernel":

@@ -179,6 +179,30 @@ def _stress_sample():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_stress_all_orders_points(precision):
+    """The stress integrands expanded to every order eps^0..eps^2 (one unit per
+    coefficient): per point against the oracle's expansion of the same integrands."""
+    need_gpu()
+    from paper_1511_03614_gb300 import prepare_direct
+    probs = W.stress_suite(40, all_orders=True)
+    prep = prepare_direct(probs, "stress")
+    assert len(prep.units) == sum(len(p.orders) for p in probs) > 100
+    integ = _integ(prep)
+    rng = np.random.default_rng(37)
+    par = Parity("stress-all-orders", precision)
+    oracle_units = {}
+    for k, p in enumerate(probs):
+        for o in P.direct_problem(p).units:
+            oracle_units[(k, o.order)] = o
+    for i, u in enumerate(prep.units):
+        o = oracle_units[(u.sector, u.order)]
+        X = sample_points(u.dim, rng, 8, n_log=4, n_edge=4)
+        f = integ.eval_batch(i, X, precision)
+        par.check(f, reference(o, X), P.magnitude_numpy(o, X), X, i)
+    par.finish(MIN_STRICT_SHARE[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_stress_points(precision):
     need_gpu()
     global _STRESS

@@ -190,7 +190,7 @@ def _monomials_up_to_degree3(dim):
     return out
 
 
-def stress_suite(n_units: int = 10_000, seed: int = STRESS_SEED, orders=(0, 1, 2)):
+def stress_suite(n_units: int = 10_000, seed: int = STRESS_SEED, orders=(0, 1, 2), all_orders: bool = False):
     """The seeded synthetic stress suite.
 
     Each integrand has dim uniform in 3..8, monomial exponents k_i in {0..3},
@@ -201,7 +201,9 @@ def stress_suite(n_units: int = 10_000, seed: int = STRESS_SEED, orders=(0, 1, 2
     log(P1)^j with j in {0, 1, 2}.  Coefficients are rounded to binary64.  Each
     integrand contributes one unit: the coefficient of eps^K with K drawn
     uniformly from ``orders`` (the lowest order when the integrand does not
-    depend on eps).  Returns a list of DirectProblem.
+    depend on eps); with ``all_orders`` it contributes the coefficients of every
+    order in ``orders`` instead (the same integrands: the order is still drawn).
+    Returns a list of DirectProblem.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
@@ -221,8 +223,10 @@ def stress_suite(n_units: int = 10_000, seed: int = STRESS_SEED, orders=(0, 1, 2
             factors.append(DirectFactor(terms=terms, n=n, m=m))
         j = int(rng.integers(0, 3))
         K = int(orders[int(rng.integers(0, len(orders)))])
-        if all(f.m == 0 for f in factors):
+        eps_free = all(f.m == 0 for f in factors)
+        if eps_free:
             K = min(orders)          # higher coefficients of an eps-free integrand vanish
+        Ks = (min(orders),) if eps_free else tuple(orders)
         out.append(DirectProblem(name=f"stress{u}", dim=dim, monomial=mono,
-                                 factors=tuple(factors), log_power=j, orders=(K,)))
+                                 factors=tuple(factors), log_power=j, orders=Ks if all_orders else (K,)))
     return out
