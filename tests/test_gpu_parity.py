@@ -67,6 +67,29 @@ def test_fused_double_box_points(precision):
     par.finish(MIN_STRICT_SHARE[precision])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_six_orders_points(precision):
+    """The largest fused unit: the box expanded to eps^3 carries six orders (the most a
+    unit holds) in most sectors; every result per point against the oracle's integrand
+    of its sector and order."""
+    need_gpu()
+    from paper_1511_03614_gb300 import prepare_feynman
+    prob = W.box(order=3)
+    prep = prepare_feynman(prob, fuse_orders=True)
+    assert max(u.n_out for u in prep.units) == 6
+    by = {(u.sector, u.order): u for u in P.feynman_problem(prob).units}
+    integ = _integ(prep)
+    rng = np.random.default_rng(38)
+    par = Parity("box-eps3-fused", precision)
+    for i, u in enumerate(prep.units):
+        X = sample_points(u.dim, rng, 24, n_log=16, n_edge=8)
+        f = integ.eval_batch(i, X, precision)
+        for k in range(u.n_out):
+            o = by[(u.sector, u.order + k)]
+            par.check(f[:, k], reference(o, X), P.magnitude_numpy(o, X), X, (i, k))
+    par.finish(MIN_STRICT_SHARE[precision])
+
+
 @pytest.mark.parametrize("accumulate,threads", [("registers", 256), ("shared", 128)])
 def test_fused_double_box_same_point_sums(accumulate, threads):
     """Iteration 0 on the uniform grid, every fused unit at once: each result's mean
