@@ -385,6 +385,15 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_tta and args.workload in ("box", "bubble", "box_physical",
                                                                          "double_box"):
         tta = time_to_accuracy(args.workload, 1e-4)
+        base = tta.get("fp64_vegas", {})
+        if cpu and base.get("points") and cpu.get("value"):
+            # the compiled CPU baseline at the same points and Vegas spec: the plain binary64
+            # run's point count (scaled to the target when it was capped) at the CPU's rate
+            need = base["points"] * (1.0 if base.get("converged") else base.get("error_over_target", 1.0) ** 2)
+            cpu["time_to_1e-4_s"] = need / cpu["value"]
+            cpu["time_to_1e-4_basis"] = ("points of the GPU's plain binary64 Vegas run"
+                                         + ("" if base.get("converged") else ", extrapolated to the target")
+                                         + " at the measured CPU rate")
 
     if rank == 0:
         line = {
@@ -476,7 +485,8 @@ def time_to_accuracy(workload, target, cap_s=15.0):
             t0 = time.perf_counter()
             ig = Integrator(prepared(workload, fuse=bool(fuse), terms=fuse == "terms"))
             r = fn(ig)
-            rec = {"gpu_s": r["gpu_s"], "converged": r["converged"], "wall_s": time.perf_counter() - t0}
+            rec = {"gpu_s": r["gpu_s"], "converged": r["converged"], "wall_s": time.perf_counter() - t0,
+                   "points": r.get("points")}
             if not r["converged"] and r.get("ratio"):
                 rec["error_over_target"] = r["ratio"]
                 rec["extrapolated_gpu_s"] = r["gpu_s"] * r["ratio"] ** 2
