@@ -16,8 +16,8 @@
 // place order), so each unit owns one contiguous run of regions and every
 // per-unit step is a fixed-order block reduction.  Per pass:
 //   k_cuhre_eval    one block per batch of a unit's regions (about CU_ITEM_PTS rule
-//                   points): one thread per (region, rule point) runs the bytecode
-//                   interpreter into a shared-memory buffer, then one warp per region
+//                   points): one thread per (region, rule point) runs the program
+//                   (micro-op form, as in k_eval) into a shared-memory buffer, then one warp per region
 //                   forms I7, I5, |I7 - I5| per result and the split axis;
 //   k_cuhre_decide  one block per unit: sums over its live regions, tolerances,
 //                   convergence; regions within their volume's share of the
@@ -97,15 +97,17 @@ __device__ __forceinline__ double cu_gen(int p, int j, int n, const CuConsts &K)
     return ((t >> (n - 1 - j)) & 1) ? -K.lam5 : K.lam5;
 }
 
+// the program in its micro-op form (uops.cuh): shared memory viewed as binary64 holds the
+// constants (then -0, 1, -1) below the per-thread region of coordinates and slot file
 struct CuSmem {
-    size_t code, cons, logtab, x, slots, f, total;
+    size_t uops, cons, logtab, x, slots, f, total;
 };
 
 __host__ __device__ inline CuSmem cu_smem(int max_instr, int max_const, int max_slots, int threads) {
     CuSmem L;
     size_t off = 0;
-    L.code = off; off = align16(off + sizeof(uint32_t) * max_instr);
-    L.cons = off; off = align16(off + sizeof(double) * (max_const > 0 ? max_const : 1));
+    L.uops = off; off = align16(off + sizeof(uint64_t) * (max_instr + 1));
+    L.cons = off; off = align16(off + sizeof(double) * (max_const + 3));
     L.logtab = off; off = align16(off + sizeof(double) * LOGTAB_DOUBLES);
     L.x = off; off = align16(off + sizeof(double) * MAXD * threads);
     L.slots = off; off = align16(off + sizeof(double) * max_slots * threads);
@@ -128,7 +130,7 @@ __global__ void k_cuhre_init(int64_t nu, double *rc, double *rh, int32_t *runit)
 // Block = item: a batch of consecutive regions of one unit (item_off: first item of
 // each unit position, reg_off: its first live region).
 __global__ void __launch_bounds__(256) k_cuhre_eval(const DevUnit *__restrict__ units, int64_t unit_begin,
-                                                    const uint32_t *__restrict__ code,
+                                                    const uint64_t *__restrict__ pre,
                                                     const double *__restrict__ cons64,
                                                     const double *__restrict__ logtab,
                                                     const int64_t *__restrict__ item_off,
@@ -149,15 +151,23 @@ __global__ void __launch_bounds__(256) k_cuhre_eval(const DevUnit *__restrict__ 
     const DevUnit u = units[unit_begin + up];
     const int nt = blockDim.x, tid = threadIdx.x;
     const CuSmem L = cu_smem(max_instr, max_const, max_slots, nt);
-    uint32_t *s_code = reinterpret_cast<uint32_t *>(smem + L.code);
+    uint64_t *s_uops = reinterpret_cast<uint64_t *>(smem + L.uops);
     double *s_cons = reinterpret_cast<double *>(smem + L.cons);
     double *s_logtab = reinterpret_cast<double *>(smem + L.logtab);
     double *s_x = reinterpret_cast<double *>(smem + L.x);
     double *s_slots = reinterpret_cast<double *>(smem + L.slots);
     double *s_f = reinterpret_cast<double *>(smem + L.f);
+    const int cons_base = static_cast<int>(L.cons / sizeof(double)), k_zero = cons_base + max_const;
+    const int pt = static_cast<int>(L.x / sizeof(double)), slot_base = static_cast<int>(L.slots / sizeof(double));
     for (int i = tid; i < LOGTAB_DOUBLES; i += nt) s_logtab[i] = logtab[i];
-    for (int i = tid; i < u.n_instr; i += nt) s_code[i] = code[u.code_off + i];
+    for (int i = tid; i < u.n_uop; i += nt) s_uops[i] = uop_from_pre(pre[u.uop_off + i], cons_base, k_zero, pt, slot_base, nt);
     for (int i = tid; i < u.n_const; i += nt) s_cons[i] = cons64[u.const_off + i];
+    if (tid == 0) {
+        s_uops[u.n_uop] = 0ull;                          // fetched after the last word, never executed
+        s_cons[max_const] = -0.0;
+        s_cons[max_const + 1] = 1.0;
+        s_cons[max_const + 2] = -1.0;
+    }
     __syncthreads();
     const int n = cu_n(u.dim), P = cu_points(n), no = u.n_out;
     const int64_t r0 = reg_off[up] + (item - item_off[up]) * cu_batch(P);
@@ -169,7 +179,7 @@ __global__ void __launch_bounds__(256) k_cuhre_eval(const DevUnit *__restrict__ 
         const double *c = rc + r * CU_STRIDE;
         const double *h = rh + r * CU_STRIDE;
         for (int j = 0; j < u.dim; ++j) s_x[j * nt + tid] = __dadd_rn(c[j], __dmul_rn(cu_gen(p, j, n, K), h[j]));
-        (void)interpret<double>(s_code, u.n_instr, s_cons, s_slots + tid, s_x + tid, nt, u.out_slot, s_logtab);
+        interpret_uop<double>(s_uops, u.n_uop, reinterpret_cast<double *>(smem), pt, tid, s_logtab);
         for (int o = 0; o < no; ++o) s_f[q * no + o] = s_slots[tid + u.outs[o] * nt];
     }
     __syncthreads();
@@ -601,7 +611,7 @@ int fiesta_cuhre(fiesta_ctx *c, const fiesta_cuhre_options *opt, double *value, 
         CUDA_TRY(cudaMemcpyAsync(S.item_off, item_off.data(), sizeof(int64_t) * (nu + 1), cudaMemcpyHostToDevice, st));
         CUDA_TRY(cudaEventRecord(p0, st));
         k_cuhre_eval<<<(unsigned)item_off[nu], threads, L.total, st>>>(
-            c->d_units, b, c->d_code, c->d_cons64, c->d_logtab, S.item_off, S.reg_off, nu, S.rc[S.cur],
+            c->d_units, b, c->d_pre, c->d_cons64, c->d_logtab, S.item_off, S.reg_off, nu, S.rc[S.cur],
             S.rh[S.cur], S.rval, S.rerr, S.raxis, K, si.max_instr, si.max_const, si.max_slots);
         launches += 1;
         eval_launches += 1;
